@@ -1,0 +1,256 @@
+/*
+ * msbicg.h - C ABI of libmsbicg: multi-shifted BiCG for Kramers-Heisenberg
+ * (RIXS) response functions on one GB300 (sm_103a).
+ *
+ * What the library computes (arXiv:2506.09551):
+ *   I(w_in, w) = (1/pi) Im <Psi|O1^dag (H - E_G - w - i eta)^{-1} O1|Psi>        (Eq. 1)
+ *   |Psi(w_in)> = (H' - E_G - w_in - i Gamma)^{-1} O2 |G>                        (Eq. 2)
+ * on a 1D Hubbard chain (Eq. 9) with a core-hole Hamiltonian (Eq. 10), O2 =
+ * c^dag_{j,up}, O1 = c_{j,up}.  All |Psi(w_in)> come from one seed Krylov
+ * recurrence shared by every incident energy (Eqs. 4-8, App. C, Alg. 1); the
+ * second step is a Lanczos continued fraction for every w_in.
+ *
+ * Conventions for every call
+ *   - Vectors are caller-owned DEVICE buffers unless stated otherwise.
+ *     Complex vectors are interleaved (re, im): 16 bytes per element for
+ *     MSB_FP64, 8 bytes for MSB_FP32_MIXED.  A block of nvec vectors is stored
+ *     vector after vector (vector k starts at element k * dim).
+ *   - Basis order: a many-body state (u, d) of the (n_up, n_dn) sector has
+ *     index rank(u) * D_dn + rank(d); rank is the position of the L-bit
+ *     occupation string among all strings of that popcount in ascending order
+ *     (bit i = site i).  Fermionic signs use the Jordan-Wigner order "all up
+ *     orbitals (site 0..L-1), then all down orbitals".
+ *   - Handles (msb_basis, msb_op) are library-owned: create/destroy pairs.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Device work is ordered on it.  Calls that return host results
+ *     synchronise the stream before returning.
+ *   - No exceptions cross the ABI: every call returns msb_status and, on
+ *     failure, sets a thread-local message readable with msb_last_error().
+ *   - There is no CPU fallback: without a usable CUDA device every compute
+ *     call returns MSB_ECUDA.
+ */
+#ifndef MSBICG_H
+#define MSBICG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MSB_OK = 0,
+    MSB_EINVAL = 1,       /* invalid argument (sizes, pointers, model)            */
+    MSB_ENOMEM = 2,       /* device or pinned-host allocation failed              */
+    MSB_ECUDA = 3,        /* CUDA runtime error, or no usable device               */
+    MSB_EBREAKDOWN = 4,   /* (p, A p) = 0, zeta_{m+1} = 0, or (r, r) = 0 with r != 0 */
+    MSB_EMAXITER = 5,     /* iteration cap reached; partial results are written    */
+    MSB_ENONFINITE = 6,   /* NaN or Inf met in a recurrence scalar                 */
+    MSB_ETIMEOUT = 7      /* reserved: a bounded device wait ran out               */
+} msb_status;
+
+typedef enum {
+    MSB_FP64 = 0,         /* complex double vectors, FP64 apply and updates         */
+    MSB_FP32_MIXED = 1    /* complex float vectors and apply; FP64 dots, zeta/alpha/
+                             beta recurrences, ground state and continued fraction */
+} msb_precision;
+
+typedef struct { double re, im; } msb_complex;
+
+/* Hubbard chain and RIXS transition (Eqs. 9-10; Sec. III).
+ * H' = H - Uc (n_{j,up} + n_{j,dn}) on the (n_up + 1, n_dn) sector: the core
+ * hole sits on the site j = core_site where O2 = c^dag_{j,up} acted, and the
+ * edge energy E_edge is absorbed into w_in. */
+typedef struct {
+    int L;            /* sites, 3 <= L <= 16 for a ring, 2 <= L <= 16 open       */
+    int n_up, n_dn;   /* electrons of the ground-state sector                    */
+    int periodic;     /* 1: ring (bond L-1 -- 0 carries sign (-1)^(N_s - 1)); 0: open */
+    double t;         /* nearest-neighbour hopping (Eq. 9)                       */
+    double U;         /* on-site repulsion (Eq. 9)                               */
+    double Uc;        /* core-hole potential (Eq. 10)                            */
+    int core_site;    /* j of O2 = c^dag_{j,up}, O1 = c_{j,up}                  */
+} msb_model;
+
+/* Parameters of the whole map (Eqs. 1-2). */
+typedef struct {
+    double Gamma;        /* inverse core-hole lifetime (Eq. 2), > 0             */
+    double eta;          /* broadening replacing i0+ in Eq. 1, > 0              */
+    double gs_tol;       /* ground state: ||H G - E_G G|| <= gs_tol max(1,|E_G|) */
+    int gs_maxit;        /* Lanczos steps per restart for the ground state       */
+    double solve_tol;    /* per shift: ||r^(w)|| <= solve_tol ||O2 G||            */
+    int maxit;           /* seed iteration cap                                   */
+    double cf_tol;       /* continued fraction: stop when no I(w) of a row moves
+                            by more than cf_tol * max_w |I| over cf_check levels */
+    int cf_check;        /* levels between convergence checks (e.g. 50)          */
+    int cf_maxdepth;     /* depth cap of the continued fraction                  */
+    int seed_index;      /* incident energy used as the seed; -1: nearest to 0   */
+    int block;           /* lag of the fused per-shift update (1..16; 0 = auto)  */
+    msb_precision precision;
+} msb_map_params;
+
+/* Counters and timings filled by the solve and map calls (any field may be 0). */
+typedef struct {
+    int iterations;             /* seed iterations = MVMs of the shared recurrence    */
+    int n_converged;            /* shifts that met the tolerance                      */
+    int64_t matvecs;            /* all operator applications (ground state, solve, CF) */
+    int64_t flushes;            /* launches of the fused per-shift update             */
+    double seed_residual;       /* ||r_m|| / ||b|| of the seed at exit                */
+    double max_shift_residual;  /* max over shifts of ||r_m|| / (|zeta_m| ||b||)      */
+    double E_G;                 /* ground-state energy used                           */
+    double gs_residual;         /* ||H G - E_G G|| of the ground state                 */
+    int cf_depth_max;           /* deepest continued fraction used                    */
+    int cf_depth_min;
+    double seconds_ground_state, seconds_solve, seconds_second_step, seconds_total;
+    int64_t device_bytes;       /* workspace bytes allocated by the call              */
+    int64_t kernel_launches;    /* kernels launched by the call                       */
+} msb_solve_info;
+
+typedef struct msb_basis msb_basis;
+typedef struct msb_op msb_op;
+
+/* ------------------------------------------------------------------------ */
+/* Diagnostics                                                               */
+/* ------------------------------------------------------------------------ */
+
+/* Message of the last failed call on this thread ("" if none).  The pointer
+ * stays valid until the next failing call on the same thread. */
+const char *msb_last_error(void);
+
+/* Library version string, e.g. "msbicg 0.1 sm_103a". */
+const char *msb_version(void);
+
+/* Fill `p` with the defaults used by the map workloads: Gamma 0.3, eta 0.1,
+ * gs_tol 1e-12, gs_maxit 300, solve_tol 1e-10, maxit 5000, cf_tol 1e-10,
+ * cf_check 50, cf_maxdepth 4000, seed_index -1, block 0, MSB_FP64. */
+void msb_map_params_default(msb_map_params *p);
+
+/* ------------------------------------------------------------------------ */
+/* Sector basis (host)                                                       */
+/* ------------------------------------------------------------------------ */
+
+/* Occupation-number basis of the (n_up, n_dn) sector of an L-site chain: the
+ * Hilbert space of Eq. (A1) in the paper's notation.  Host-only object.
+ * Errors: MSB_EINVAL if L is outside 1..16 or n outside 0..L. */
+msb_status msb_basis_create(int L, int n_up, int n_dn, msb_basis **out);
+
+/* Sizes: D_up = C(L, n_up), D_dn = C(L, n_dn), dim = D_up * D_dn (any output may be NULL). */
+msb_status msb_basis_dims(const msb_basis *b, int64_t *D_up, int64_t *D_dn, int64_t *dim);
+
+/* Copy the occupation strings of one spin species (0 = up, 1 = down) in rank
+ * order into the HOST array `out` (D_species entries). */
+msb_status msb_basis_states(const msb_basis *b, int species, uint32_t *out);
+
+void msb_basis_destroy(msb_basis *b);
+
+/* ------------------------------------------------------------------------ */
+/* Operators A = H, H' (matrix-free) or a user CSR matrix                    */
+/* ------------------------------------------------------------------------ */
+
+/* Matrix-free Hubbard operator.  intermediate = 0: H of Eq. (9) on the
+ * (n_up, n_dn) sector; intermediate = 1: H' of Eq. (10) on (n_up + 1, n_dn).
+ * The hopping tables are built on the host and copied to the current device.
+ * Errors: MSB_EINVAL (model out of range), MSB_ECUDA, MSB_ENOMEM. */
+msb_status msb_op_create_hubbard(const msb_model *model, int intermediate, msb_op **out);
+
+/* General real symmetric sparse matrix in CSR form (HOST arrays: rowptr[n+1],
+ * col[nnz], val[nnz]); copied to the device.  Symmetry is assumed, not checked;
+ * the solver needs A^T = A (App. A).  Columns must lie in [0, n). */
+msb_status msb_op_create_csr(int64_t n, const int64_t *rowptr, const int32_t *col,
+                             const double *val, msb_op **out);
+
+msb_status msb_op_dim(const msb_op *op, int64_t *dim);
+
+void msb_op_destroy(msb_op *op);
+
+/* y_k = (A + c0 I) x_k for k < nvec (the MVM of Alg. 1).  x and y are device
+ * blocks of nvec complex vectors (FP64 or FP32 by `prec`); x and y must not
+ * overlap.  Asynchronous on `stream`. */
+msb_status msb_op_apply(msb_op *op, msb_complex c0, const void *x, void *y, int nvec,
+                        msb_precision prec, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Transition operators between sectors (Eqs. 1-2 with the dipole operators  */
+/* reduced to a single orbital)                                              */
+/* ------------------------------------------------------------------------ */
+
+/* y_k = c^dag_{site,up} x_k: x in the (n_up, n_dn) sector of `model`, y in
+ * (n_up + 1, n_dn).  Complex vectors per `prec`; asynchronous. */
+msb_status msb_apply_cdag_up(const msb_model *model, int site, const void *x, void *y,
+                             int nvec, msb_precision prec, void *stream);
+
+/* y_k = c_{site,up} x_k: x in (n_up + 1, n_dn), y in (n_up, n_dn). */
+msb_status msb_apply_c_up(const msb_model *model, int site, const void *x, void *y,
+                          int nvec, msb_precision prec, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Ground state (Sec. III: |G>, E_G; Lanczos in FP64 in every mode)         */
+/* ------------------------------------------------------------------------ */
+
+/* Lowest eigenpair of the real symmetric operator H by Lanczos, restarted from
+ * its Ritz vector until ||H g - E g|| <= tol * max(1, |E|).  `start` is an
+ * optional device real vector (NULL: a counter-based pseudo-random vector);
+ * `g` is a device real double vector of length dim (caller-owned, output,
+ * unit norm).  E_G and residual are host outputs.  Synchronises `stream`.
+ * Errors: MSB_EMAXITER if 20 restarts do not reach tol (g, E_G still written). */
+msb_status msb_ground_state(msb_op *H, double tol, int maxit, const double *start,
+                            double *E_G, double *g, double *residual, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Multi-shifted BiCG (App. C; Alg. 1 in corrected form)                     */
+/* ------------------------------------------------------------------------ */
+
+/* Solve (A + c0 I - s_k I) x_k = b for every shift s_k (HOST array, n_shifts
+ * <= 4096) from one seed recurrence on A + c0 I, which must be complex
+ * symmetric (real symmetric A; c0 complex).  b: device complex vector; x:
+ * device block of n_shifts complex vectors (caller-owned, output).  A shift is
+ * frozen once ||r_m|| / |zeta_m^(k)| <= tol ||b||.  Optional HOST outputs
+ * (may be NULL): iters[k], resid[k] (that ratio / ||b|| at freeze), converged[k].
+ * `block` (1..16, 0 = auto) lags the fused per-shift update: the vectors
+ * p^(k), x^(k) are advanced once every `block` iterations from the stored seed
+ * residuals, with coefficients from the same recurrences.
+ * Returns MSB_EMAXITER (results still written) if a shift did not converge
+ * within maxit, MSB_EBREAKDOWN / MSB_ENONFINITE on a failed recurrence. */
+msb_status msb_multishift_bicg_solve(msb_op *A, msb_complex c0, const void *b,
+                                     const msb_complex *shifts, int n_shifts, double tol,
+                                     int maxit, int block, msb_precision prec, void *x,
+                                     int *iters, double *resid, int *converged,
+                                     msb_solve_info *info, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Second step: batched Lanczos continued fraction (Eq. 1; Sec. III)         */
+/* ------------------------------------------------------------------------ */
+
+/* For each of n_vec device complex vectors phi_k (block, per `prec`) of the
+ * space of the real symmetric operator H, compute
+ *   I[k][i] = (1/pi) Im <phi_k|(H - E0 - w_i - i eta)^{-1}|phi_k>
+ * by a Hermitian Lanczos continued fraction of converged depth (see
+ * msb_map_params.cf_tol / cf_check / cf_maxdepth).  I_out is a HOST array
+ * n_vec x n_w; depth (HOST, nullable) receives each row's depth.
+ * The input vectors are not modified.  Synchronises `stream`. */
+msb_status msb_continued_fraction(msb_op *H, const void *phi, int n_vec, double E0,
+                                  const double *w, int n_w, double eta, double cf_tol,
+                                  int cf_check, int cf_maxdepth, msb_precision prec,
+                                  double *I_out, int *depth, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* The whole RIXS map (Eqs. 1-2)                                             */
+/* ------------------------------------------------------------------------ */
+
+/* I_out[k][i] = I(w_in[k], w[i]) for the model, HOST arrays w_in[n_in], w[n_w]
+ * and HOST output I_out[n_in * n_w].  G: optional device real unit vector of
+ * the ground sector with energy E_G (NULL: computed by msb_ground_state with
+ * params->gs_tol).  The seed system is w_in[seed_index]; the shifts are
+ * w_in[k] - w_in[seed].  Synchronises `stream`; all workspace is allocated
+ * and freed inside the call.  Returns MSB_EMAXITER if some w_in did not
+ * converge (the map is still written). */
+msb_status msb_rixs_map(const msb_model *model, const msb_map_params *params,
+                        const double *G, double E_G, const double *w_in, int n_in,
+                        const double *w, int n_w, double *I_out, msb_solve_info *info,
+                        void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MSBICG_H */

@@ -1,0 +1,185 @@
+"""Torch / numpy front end of libmsbicg: argument marshalling only.
+
+Device vectors are torch tensors on the current CUDA device (complex128 for
+MSB_FP64, complex64 for MSB_FP32_MIXED; the ground state is float64); every
+call runs on torch's current stream.  All arithmetic happens in the library.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import native as N
+
+FP64, FP32_MIXED = N.MSB_FP64, N.MSB_FP32_MIXED
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t: torch.Tensor):
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def cdtype(prec: int) -> torch.dtype:
+    return torch.complex128 if prec == FP64 else torch.complex64
+
+
+def model(L, n_up, n_dn, t=1.0, U=8.0, Uc=4.0, core_site=0, periodic=True) -> N.msb_model:
+    return N.msb_model(L, n_up, n_dn, 1 if periodic else 0, t, U, Uc, core_site)
+
+
+def map_params(**kw) -> N.msb_map_params:
+    p = N.msb_map_params()
+    N.load().msb_map_params_default(C.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def basis_states(L: int, n_up: int, n_dn: int):
+    lib = N.load()
+    h = C.c_void_p()
+    N.check(lib.msb_basis_create(L, n_up, n_dn, C.byref(h)))
+    try:
+        du, dd, dim = C.c_int64(), C.c_int64(), C.c_int64()
+        N.check(lib.msb_basis_dims(h, C.byref(du), C.byref(dd), C.byref(dim)))
+        up = np.zeros(du.value, dtype=np.uint32)
+        dn = np.zeros(dd.value, dtype=np.uint32)
+        N.check(lib.msb_basis_states(h, 0, up.ctypes.data_as(C.POINTER(C.c_uint32))))
+        N.check(lib.msb_basis_states(h, 1, dn.ctypes.data_as(C.POINTER(C.c_uint32))))
+        return up, dn
+    finally:
+        lib.msb_basis_destroy(h)
+
+
+class Operator:
+    """Handle of a library operator (matrix-free Hubbard H / H', or CSR)."""
+
+    def __init__(self, handle: C.c_void_p):
+        self.h = handle
+        d = C.c_int64()
+        N.check(N.load().msb_op_dim(self.h, C.byref(d)))
+        self.dim = d.value
+
+    @classmethod
+    def hubbard(cls, m: N.msb_model, intermediate: bool = False) -> "Operator":
+        h = C.c_void_p()
+        N.check(N.load().msb_op_create_hubbard(C.byref(m), 1 if intermediate else 0, C.byref(h)))
+        return cls(h)
+
+    @classmethod
+    def csr(cls, rowptr: np.ndarray, col: np.ndarray, val: np.ndarray) -> "Operator":
+        rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+        col = np.ascontiguousarray(col, dtype=np.int32)
+        val = np.ascontiguousarray(val, dtype=np.float64)
+        h = C.c_void_p()
+        N.check(N.load().msb_op_create_csr(len(rowptr) - 1, rowptr.ctypes.data_as(C.POINTER(C.c_int64)),
+                                           col.ctypes.data_as(C.POINTER(C.c_int32)),
+                                           val.ctypes.data_as(C.POINTER(C.c_double)), C.byref(h)))
+        return cls(h)
+
+    def close(self):
+        if self.h:
+            N.load().msb_op_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def apply(self, x: torch.Tensor, c0: complex = 0.0, prec: int | None = None, out: torch.Tensor | None = None):
+        """y = (A + c0) x; x of shape (dim,) or (nvec, dim)."""
+        if prec is None:
+            prec = FP64 if x.dtype == torch.complex128 else FP32_MIXED
+        if x.dtype != cdtype(prec):
+            raise ValueError("dtype does not match precision")
+        nvec = 1 if x.dim() == 1 else x.shape[0]
+        if x.shape[-1] != self.dim:
+            raise ValueError("length does not match the operator dimension")
+        y = torch.empty_like(x) if out is None else out
+        N.check(N.load().msb_op_apply(self.h, N.msb_complex(complex(c0).real, complex(c0).imag), _ptr(x), _ptr(y),
+                                      nvec, prec, _stream()))
+        return y
+
+    def ground_state(self, tol: float = 1e-12, maxit: int = 300, start: torch.Tensor | None = None):
+        g = torch.empty(self.dim, dtype=torch.float64, device="cuda")
+        E, res = C.c_double(), C.c_double()
+        st = _ptr(start) if start is not None else None
+        N.check(N.load().msb_ground_state(self.h, tol, maxit, st, C.byref(E), _ptr(g), C.byref(res), _stream()))
+        return E.value, g, res.value
+
+    def multishift_solve(self, b: torch.Tensor, shifts, c0: complex = 0.0, tol: float = 1e-10, maxit: int = 5000,
+                         block: int = 0, prec: int = FP64, allow_status=()):
+        """x_k = (A + c0 - s_k)^{-1} b for every shift.  Returns (x, per-shift dict, info dict, status)."""
+        shifts = np.asarray(shifts, dtype=np.complex128)
+        ns = len(shifts)
+        sh = (N.msb_complex * ns)(*[N.msb_complex(s.real, s.imag) for s in shifts])
+        x = torch.empty((ns, self.dim), dtype=cdtype(prec), device="cuda")
+        iters = np.zeros(ns, dtype=np.int32)
+        resid = np.zeros(ns, dtype=np.float64)
+        conv = np.zeros(ns, dtype=np.int32)
+        info = N.msb_solve_info()
+        c0 = complex(c0)
+        st = N.load().msb_multishift_bicg_solve(
+            self.h, N.msb_complex(c0.real, c0.imag), _ptr(b.to(cdtype(prec)).contiguous()), sh, ns, tol, maxit,
+            block, prec, _ptr(x), iters.ctypes.data_as(C.POINTER(C.c_int)),
+            resid.ctypes.data_as(C.POINTER(C.c_double)), conv.ctypes.data_as(C.POINTER(C.c_int)), C.byref(info),
+            _stream())
+        N.check(st, allow=allow_status)
+        return x, dict(iters=iters, resid=resid, converged=conv.astype(bool)), info.as_dict(), st
+
+    def continued_fraction(self, phi: torch.Tensor, E0: float, w, eta: float, cf_tol: float = 1e-10,
+                           cf_check: int = 50, cf_maxdepth: int = 4000, prec: int | None = None):
+        if prec is None:
+            prec = FP64 if phi.dtype == torch.complex128 else FP32_MIXED
+        w = np.ascontiguousarray(w, dtype=np.float64)
+        nv = 1 if phi.dim() == 1 else phi.shape[0]
+        I = np.zeros((nv, len(w)), dtype=np.float64)
+        depth = np.zeros(nv, dtype=np.int32)
+        N.check(N.load().msb_continued_fraction(self.h, _ptr(phi), nv, E0, w.ctypes.data_as(C.POINTER(C.c_double)),
+                                                len(w), eta, cf_tol, cf_check, cf_maxdepth, prec,
+                                                I.ctypes.data_as(C.POINTER(C.c_double)),
+                                                depth.ctypes.data_as(C.POINTER(C.c_int)), _stream()))
+        return I, depth
+
+
+def apply_cdag_up(m: N.msb_model, site: int, x: torch.Tensor, out_dim: int, prec: int = FP64):
+    nvec = 1 if x.dim() == 1 else x.shape[0]
+    y = torch.empty((nvec, out_dim) if x.dim() > 1 else (out_dim,), dtype=x.dtype, device="cuda")
+    N.check(N.load().msb_apply_cdag_up(C.byref(m), site, _ptr(x), _ptr(y), nvec, prec, _stream()))
+    return y
+
+
+def apply_c_up(m: N.msb_model, site: int, x: torch.Tensor, out_dim: int, prec: int = FP64):
+    nvec = 1 if x.dim() == 1 else x.shape[0]
+    y = torch.empty((nvec, out_dim) if x.dim() > 1 else (out_dim,), dtype=x.dtype, device="cuda")
+    N.check(N.load().msb_apply_c_up(C.byref(m), site, _ptr(x), _ptr(y), nvec, prec, _stream()))
+    return y
+
+
+def rixs_map(m: N.msb_model, params: N.msb_map_params, w_in, w, G: torch.Tensor | None = None, E_G: float = 0.0,
+             allow_status=(N.MSB_EMAXITER,)):
+    """The RIXS map I[n_in, n_w] (numpy), the solve info (dict) and the status."""
+    w_in = np.ascontiguousarray(w_in, dtype=np.float64)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    I = np.zeros((len(w_in), len(w)), dtype=np.float64)
+    info = N.msb_solve_info()
+    st = N.load().msb_rixs_map(C.byref(m), C.byref(params), _ptr(G) if G is not None else None, E_G,
+                               w_in.ctypes.data_as(C.POINTER(C.c_double)), len(w_in),
+                               w.ctypes.data_as(C.POINTER(C.c_double)), len(w),
+                               I.ctypes.data_as(C.POINTER(C.c_double)), C.byref(info), _stream())
+    N.check(st, allow=allow_status)
+    return I, info.as_dict(), st

@@ -1,0 +1,74 @@
+// Device helpers shared by the solver, Lanczos and map kernels.
+#pragma once
+
+#include <functional>
+
+#include "operator.cuh"
+
+namespace msb {
+
+// c * v for a complex scalar c = (cr, ci): complex v -> complex product;
+// real v -> cr * v (callers pass ci = 0 for real vectors).
+__device__ __forceinline__ double2 cscale(double cr, double ci, double2 v) {
+    return make_double2(cr * v.x - ci * v.y, cr * v.y + ci * v.x);
+}
+__device__ __forceinline__ float2 cscale(double cr, double ci, float2 v) {
+    const float a = float(cr), b = float(ci);
+    return make_float2(a * v.x - b * v.y, a * v.y + b * v.x);
+}
+__device__ __forceinline__ double cscale(double cr, double, double v) { return cr * v; }
+__device__ __forceinline__ float cscale(double cr, double, float v) { return float(cr) * v; }
+
+// Bilinear product term u * v (no conjugation) accumulated into (re, im) in FP64.
+__device__ __forceinline__ void bil_acc(double2 u, double2 v, double& re, double& im) {
+    re = fma(u.x, v.x, fma(-u.y, v.y, re));
+    im = fma(u.x, v.y, fma(u.y, v.x, im));
+}
+// FP32 operands: the product of two floats is exact in double.
+__device__ __forceinline__ void bil_acc(float2 u, float2 v, double& re, double& im) {
+    bil_acc(make_double2(u.x, u.y), make_double2(v.x, v.y), re, im);
+}
+// Hermitian product term conj(u) * v accumulated into (re, im).
+__device__ __forceinline__ void her_acc(double2 u, double2 v, double& re, double& im) {
+    re = fma(u.x, v.x, fma(u.y, v.y, re));
+    im = fma(u.x, v.y, fma(-u.y, v.x, im));
+}
+__device__ __forceinline__ void her_acc(float2 u, float2 v, double& re, double& im) {
+    her_acc(make_double2(u.x, u.y), make_double2(v.x, v.y), re, im);
+}
+__device__ __forceinline__ double norm2(double2 u) { return fma(u.x, u.x, u.y * u.y); }
+__device__ __forceinline__ double norm2(float2 u) {
+    const double a = u.x, b = u.y;
+    return fma(a, a, b * b);
+}
+__device__ __forceinline__ double norm2(double u) { return u * u; }
+
+// Sum of the n partials written by a producer kernel (stride NV, component i),
+// computed by one CTA in a fixed order.  Result valid in thread 0.
+template <int NV>
+__device__ __forceinline__ void reduce_partials(const double* part, int n, double (&out)[NV], double* sm) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) out[i] = 0.0;
+    for (int b = threadIdx.x; b < n; b += blockDim.x) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) out[i] += part[int64_t(b) * NV + i];
+    }
+    block_sum<NV>(out, sm);
+}
+
+// Store per-block partials (thread 0 holds the block sum after block_sum).
+template <int NV>
+__device__ __forceinline__ void store_partials(double (&v)[NV], double* sm, double* part) {
+    block_sum<NV>(v, sm);
+    if (threadIdx.x == 0) {
+        const int64_t base = (int64_t(blockIdx.y) * gridDim.x + blockIdx.x) * NV;
+#pragma unroll
+        for (int i = 0; i < NV; ++i) part[base + i] = v[i];
+    }
+}
+
+// CUDA device sanity check used by every compute entry point.
+void require_device();
+msb_status guard(const char* fn, const std::function<void()>& body);
+
+}  // namespace msb

@@ -1,0 +1,103 @@
+// Internal interfaces between the solver, the Lanczos routines and the map.
+#pragma once
+
+#include <vector>
+
+#include "kernels.cuh"
+
+namespace msb {
+
+constexpr int kMaxShifts = 4096;
+
+// Per-shift device arrays of the multi-shift recurrence.
+struct ShiftArrays {
+    double2* zeta;        // zeta^k_m
+    double2* zeta_prev;   // zeta^k_{m-1}
+    double2* shift;       // s_k
+    double2* coef64;      // [k][B][2]: (gamma, c) of each iteration of the block, FP64
+    void* coefv;          // same in the vector precision (double2 or float2)
+    int* active;          // 1 while the shift iterates
+    int* conv;            // 1 once it met the tolerance
+    int* broken;          // 1 if zeta_{m+1} = 0 stopped it
+    int* nblk;            // iterations of the current block to apply
+    int* iters;           // iteration at freeze
+    double* resid;        // ||r_m|| / (|zeta_m| ||b||) at freeze
+};
+
+struct SolveProblem {
+    int64_t n = 0;            // seed dimension
+    int ns = 0;               // shifts
+    const void* b = nullptr;  // device RHS (precision of prec)
+    void* x = nullptr;        // device output, ns x n_out
+    int64_t n_out = 0;        // per-shift vector length (n, or the projected length)
+    const int32_t* rows = nullptr;   // optional row map for the projected output
+    int64_t rowlen = 1;
+    double2 c0{0, 0};
+    std::vector<double2> shifts;
+    double tol = 1e-10;
+    int maxit = 1000;
+    int block = 4;
+    msb_precision prec = MSB_FP64;
+};
+
+struct SolveResult {
+    int iterations = 0;
+    int n_converged = 0;
+    int64_t flushes = 0;
+    int64_t launches = 0;
+    double seed_residual = 0, bnorm = 0;
+    std::vector<int> iters, conv;
+    std::vector<double> resid;
+    msb_status status = MSB_OK;
+};
+
+void multishift_solve(msb_op* op, const SolveProblem& pr, SolveResult& out, cudaStream_t st);
+int pick_block(int block, msb_precision prec);
+
+// Ground state by Lanczos (FP64, real vectors).
+struct GroundResult {
+    double E = 0, residual = 0;
+    int restarts = 0;
+    int64_t matvecs = 0;
+    int64_t launches = 0;
+    msb_status status = MSB_OK;
+};
+void ground_state(msb_op* H, double tol, int maxit, const double* start, double* g, GroundResult& out,
+                  cudaStream_t st);
+
+// Batched Lanczos continued fraction over n_vec columns.
+struct CFResult {
+    std::vector<int> depth;
+    int64_t matvecs = 0;
+    int64_t launches = 0;
+};
+void continued_fraction(msb_op* H, const void* phi, int n_vec, double E0, const double* w, int n_w,
+                        double eta, double cf_tol, int cf_check, int cf_maxdepth, msb_precision prec,
+                        double* I_out, CFResult& out, cudaStream_t st);
+
+// Work runs on an internal non-blocking stream ordered after the caller's
+// stream; finish() orders the caller's stream after it and synchronises.
+struct StreamScope {
+    cudaStream_t user, s;
+    cudaEvent_t ev;
+    explicit StreamScope(cudaStream_t u) : user(u) {
+        MSB_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+        MSB_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        MSB_CUDA(cudaEventRecord(ev, user));
+        MSB_CUDA(cudaStreamWaitEvent(s, ev, 0));
+    }
+    void finish() {
+        MSB_CUDA(cudaEventRecord(ev, s));
+        MSB_CUDA(cudaStreamWaitEvent(user, ev, 0));
+        MSB_CUDA(cudaStreamSynchronize(s));
+    }
+    ~StreamScope() {
+        cudaStreamSynchronize(s);
+        cudaEventDestroy(ev);
+        cudaStreamDestroy(s);
+    }
+};
+
+void set_error_message(const std::string& m);
+
+}  // namespace msb

@@ -1,0 +1,145 @@
+// Operator objects and the plain apply y = (A + c0) x (the MVM of Alg. 1).
+#include <memory>
+
+#include "operator.cuh"
+#include "kernels.cuh"
+
+namespace msb {
+
+static void build_hubbard(msb_op* op, const msb_model& m, int intermediate) {
+    validate_model(m);
+    MSB_REQUIRE(!intermediate || m.n_up + 1 <= m.L, "intermediate sector needs n_up + 1 <= L");
+    op->kind = 0;
+    op->model = m;
+    op->intermediate = intermediate;
+    op->sec_up = m.n_up + (intermediate ? 1 : 0);
+    op->sec_dn = m.n_dn;
+    op->host_up = sector_states(m.L, op->sec_up);
+    op->host_dn = sector_states(m.L, op->sec_dn);
+    std::vector<int32_t> tu, td;
+    std::vector<uint8_t> cu, cd;
+    int Wu = 0, Wd = 0;
+    hop_table(m.L, op->sec_up, m.periodic != 0, op->host_up, tu, cu, Wu);
+    hop_table(m.L, op->sec_dn, m.periodic != 0, op->host_dn, td, cd, Wd);
+    MSB_CUDA(cudaGetDevice(&op->device));
+    op->hup.alloc(tu.size()); op->hup.upload(tu.data(), tu.size());
+    op->hdn.alloc(td.size()); op->hdn.upload(td.data(), td.size());
+    op->nup.alloc(cu.size()); op->nup.upload(cu.data(), cu.size());
+    op->ndn.alloc(cd.size()); op->ndn.upload(cd.data(), cd.size());
+    op->sup.alloc(op->host_up.size()); op->sup.upload(op->host_up.data(), op->host_up.size());
+    op->sdn.alloc(op->host_dn.size()); op->sdn.upload(op->host_dn.data(), op->host_dn.size());
+    MSB_CUDA(cudaDeviceSynchronize());
+    HubView& h = op->hub;
+    h.Dup = int64_t(op->host_up.size());
+    h.Ddn = int64_t(op->host_dn.size());
+    h.Wup = Wu;
+    h.Wdn = Wd;
+    h.hup = op->hup.p; h.hdn = op->hdn.p;
+    h.nup = op->nup.p; h.ndn = op->ndn.p;
+    h.sup = op->sup.p; h.sdn = op->sdn.p;
+    h.t = m.t; h.U = m.U; h.Uc = m.Uc;
+    h.core = intermediate ? m.core_site : -1;
+    op->dim = h.Dup * h.Ddn;
+}
+
+static void build_csr(msb_op* op, int64_t n, const int64_t* rowptr, const int32_t* col,
+                      const double* val) {
+    MSB_REQUIRE(n > 0 && rowptr && col && val, "invalid CSR arguments");
+    MSB_REQUIRE(rowptr[0] == 0, "rowptr[0] must be 0");
+    const int64_t nnz = rowptr[n];
+    MSB_REQUIRE(nnz >= 0, "rowptr[n] must be >= 0");
+    for (int64_t i = 0; i < n; ++i) MSB_REQUIRE(rowptr[i + 1] >= rowptr[i], "rowptr must be non-decreasing");
+    for (int64_t k = 0; k < nnz; ++k) MSB_REQUIRE(col[k] >= 0 && col[k] < n, "column index out of range");
+    op->kind = 1;
+    op->dim = n;
+    MSB_CUDA(cudaGetDevice(&op->device));
+    op->rowptr.alloc(size_t(n + 1)); op->rowptr.upload(rowptr, size_t(n + 1));
+    op->col.alloc(size_t(nnz)); op->col.upload(col, size_t(nnz));
+    op->val64.alloc(size_t(nnz)); op->val64.upload(val, size_t(nnz));
+    std::vector<float> v32(val, val + nnz);
+    for (int64_t k = 0; k < nnz; ++k) v32[k] = float(val[k]);
+    op->val32.alloc(size_t(nnz)); op->val32.upload(v32.data(), size_t(nnz));
+    MSB_CUDA(cudaDeviceSynchronize());
+    op->csr = CsrView{n, op->rowptr.p, op->col.p, op->val64.p, op->val32.p};
+}
+
+// ---------------------------------------------------------------------------
+// y_c = (A + c0) x_c for every column c = blockIdx.y.
+// ---------------------------------------------------------------------------
+template <class View, typename V>
+__global__ void __launch_bounds__(256) k_apply(View op, const V* __restrict__ x, V* __restrict__ y,
+                                               int64_t n, double c0r, double c0i) {
+    const V* __restrict__ xc = x + int64_t(blockIdx.y) * n;
+    V* __restrict__ yc = y + int64_t(blockIdx.y) * n;
+    for (int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < n;
+         s += int64_t(gridDim.x) * blockDim.x) {
+        const V xs = xc[s];
+        const V h = op.hx(s, xc, xs);
+        yc[s] = vadd(h, cscale(c0r, c0i, xs));
+    }
+}
+
+template <class View>
+static void launch_apply(const View& v, int64_t n, double2 c0, const void* x, void* y, int nvec,
+                         msb_precision prec, cudaStream_t st) {
+    dim3 grid(grid_for(n, 256, 8), nvec);
+    if (prec == MSB_FP64)
+        k_apply<View, double2><<<grid, 256, 0, st>>>(v, (const double2*)x, (double2*)y, n, c0.x, c0.y);
+    else
+        k_apply<View, float2><<<grid, 256, 0, st>>>(v, (const float2*)x, (float2*)y, n, c0.x, c0.y);
+    MSB_LAUNCH_CHECK();
+    count_launch();
+}
+
+void op_apply(msb_op* op, double2 c0, const void* x, void* y, int nvec, msb_precision prec,
+              cudaStream_t st) {
+    MSB_REQUIRE(op != nullptr, "operator is NULL");
+    MSB_REQUIRE(x != nullptr && y != nullptr, "x / y is NULL");
+    MSB_REQUIRE(nvec >= 1 && nvec <= 65535, "nvec must be in 1..65535");
+    MSB_REQUIRE(prec == MSB_FP64 || prec == MSB_FP32_MIXED, "unknown precision");
+    if (op->kind == 0) launch_apply(op->hub, op->dim, c0, x, y, nvec, prec, st);
+    else launch_apply(op->csr, op->dim, c0, x, y, nvec, prec, st);
+}
+
+}  // namespace msb
+
+// ----------------------------------------------------------------------------
+// C ABI: operators
+// ----------------------------------------------------------------------------
+extern "C" msb_status msb_op_create_hubbard(const msb_model* model, int intermediate, msb_op** out) {
+    return msb::guard("msb_op_create_hubbard", [&] {
+        MSB_REQUIRE(model != nullptr && out != nullptr, "NULL argument");
+        msb::require_device();
+        auto op = std::make_unique<msb_op>();
+        msb::build_hubbard(op.get(), *model, intermediate ? 1 : 0);
+        *out = op.release();
+    });
+}
+
+extern "C" msb_status msb_op_create_csr(int64_t n, const int64_t* rowptr, const int32_t* col,
+                                        const double* val, msb_op** out) {
+    return msb::guard("msb_op_create_csr", [&] {
+        MSB_REQUIRE(out != nullptr, "out is NULL");
+        msb::require_device();
+        auto op = std::make_unique<msb_op>();
+        msb::build_csr(op.get(), n, rowptr, col, val);
+        *out = op.release();
+    });
+}
+
+extern "C" msb_status msb_op_dim(const msb_op* op, int64_t* dim) {
+    return msb::guard("msb_op_dim", [&] {
+        MSB_REQUIRE(op != nullptr && dim != nullptr, "NULL argument");
+        *dim = op->dim;
+    });
+}
+
+extern "C" void msb_op_destroy(msb_op* op) { delete op; }
+
+extern "C" msb_status msb_op_apply(msb_op* op, msb_complex c0, const void* x, void* y, int nvec,
+                                   msb_precision prec, void* stream) {
+    return msb::guard("msb_op_apply", [&] {
+        msb::require_device();
+        msb::op_apply(op, make_double2(c0.re, c0.im), x, y, nvec, prec, (cudaStream_t)stream);
+    });
+}

@@ -1,0 +1,166 @@
+// Operators of the solver: the matrix-free Hubbard Hamiltonian H / H'
+// (Eqs. 9-10) on a bit-string sector basis, and a general real symmetric CSR
+// matrix.  Both expose a device "view" with one method,
+//     V hx(s, x, xs)  =  (A x)[s]      (xs = x[s], already loaded)
+// which every apply-style kernel (plain apply, seed MVM with fused bilinear
+// product, Lanczos step with fused Hermitian product) calls per element.
+#pragma once
+
+#include <type_traits>
+
+#include "common.cuh"
+
+namespace msb {
+
+// ---- value-type helpers: V is double, float (real vectors) or double2,
+// float2 (complex vectors); S is the matching real scalar. ----
+__device__ __forceinline__ double vzero(double) { return 0.0; }
+__device__ __forceinline__ float vzero(float) { return 0.0f; }
+__device__ __forceinline__ double2 vzero(double2) { return make_double2(0.0, 0.0); }
+__device__ __forceinline__ float2 vzero(float2) { return make_float2(0.f, 0.f); }
+__device__ __forceinline__ double vadd(double a, double b) { return a + b; }
+__device__ __forceinline__ float vadd(float a, float b) { return a + b; }
+__device__ __forceinline__ double2 vadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double vsub(double a, double b) { return a - b; }
+__device__ __forceinline__ float vsub(float a, float b) { return a - b; }
+__device__ __forceinline__ double2 vsub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 vsub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// a * v + acc (real a)
+__device__ __forceinline__ double vaxpy(double a, double v, double acc) { return fma(a, v, acc); }
+__device__ __forceinline__ float vaxpy(float a, float v, float acc) { return fmaf(a, v, acc); }
+__device__ __forceinline__ double2 vaxpy(double a, double2 v, double2 acc) {
+    return make_double2(fma(a, v.x, acc.x), fma(a, v.y, acc.y));
+}
+__device__ __forceinline__ float2 vaxpy(float a, float2 v, float2 acc) {
+    return make_float2(fmaf(a, v.x, acc.x), fmaf(a, v.y, acc.y));
+}
+__device__ __forceinline__ double vscale(double a, double v) { return a * v; }
+__device__ __forceinline__ float vscale(float a, float v) { return a * v; }
+__device__ __forceinline__ double2 vscale(double a, double2 v) { return make_double2(a * v.x, a * v.y); }
+__device__ __forceinline__ float2 vscale(float a, float2 v) { return make_float2(a * v.x, a * v.y); }
+
+template <typename V> struct Scalar;
+template <> struct Scalar<double> { using type = double; };
+template <> struct Scalar<float> { using type = float; };
+template <> struct Scalar<double2> { using type = double; };
+template <> struct Scalar<float2> { using type = float; };
+template <typename V> using scalar_t = typename Scalar<V>::type;
+template <typename V>
+constexpr bool is_cplx_v = std::is_same<V, double2>::value || std::is_same<V, float2>::value;
+
+// ----------------------------------------------------------------------------
+// Hubbard view.  Basis index s = iu * Ddn + id.  Hop tables are ELL with the
+// hop slot as the slow index ([slot][state]) so that consecutive threads
+// (consecutive id) read consecutive entries.  An entry is
+// (target_rank << 1) | (sign < 0), -1 when empty; valid entries come first
+// and n{up,dn}[state] counts them.  The matrix element of a hop is -t * sign.
+// ----------------------------------------------------------------------------
+struct HubView {
+    int64_t Dup, Ddn;
+    int Wup, Wdn;
+    const int32_t* hup;
+    const int32_t* hdn;
+    const uint8_t* nup;
+    const uint8_t* ndn;
+    const uint32_t* sup;   // occupation strings, rank order
+    const uint32_t* sdn;
+    double t, U, Uc;
+    int core;              // core-hole site, -1: none (plain H)
+
+    __device__ __forceinline__ double diag(int64_t iu, int64_t id) const {
+        const uint32_t a = __ldg(sup + iu), b = __ldg(sdn + id);
+        double v = U * double(__popc(a & b));
+        if (core >= 0) v -= Uc * double(((a >> core) & 1u) + ((b >> core) & 1u));
+        return v;
+    }
+
+    template <typename V>
+    __device__ __forceinline__ V hx_at(int64_t iu, int64_t id, const V* __restrict__ x, V xs) const {
+        using S = scalar_t<V>;
+        V acc = vzero(xs);
+        const int nu = __ldg(nup + iu);
+        for (int e = 0; e < nu; ++e) {
+            const int32_t h = __ldg(hup + int64_t(e) * Dup + iu);
+            const V v = x[int64_t(h >> 1) * Ddn + id];
+            acc = (h & 1) ? vsub(acc, v) : vadd(acc, v);
+        }
+        const int nd = __ldg(ndn + id);
+        const V* __restrict__ xrow = x + iu * Ddn;
+        for (int e = 0; e < nd; ++e) {
+            const int32_t h = __ldg(hdn + int64_t(e) * Ddn + id);
+            const V v = xrow[h >> 1];
+            acc = (h & 1) ? vsub(acc, v) : vadd(acc, v);
+        }
+        // H x = diag * x - t * sum(sign * x_neighbour)
+        return vaxpy(S(-t), acc, vscale(S(diag(iu, id)), xs));
+    }
+
+    template <typename V>
+    __device__ __forceinline__ V hx(int64_t s, const V* __restrict__ x, V xs) const {
+        const int64_t iu = s / Ddn, id = s - iu * Ddn;
+        return hx_at(iu, id, x, xs);
+    }
+};
+
+// ----------------------------------------------------------------------------
+// CSR view of a real symmetric matrix (val in the vector's scalar precision).
+// ----------------------------------------------------------------------------
+struct CsrView {
+    int64_t n;
+    const int64_t* rowptr;
+    const int32_t* col;
+    const double* val64;
+    const float* val32;
+
+    template <typename V>
+    __device__ __forceinline__ V hx(int64_t s, const V* __restrict__ x, V xs) const {
+        using S = scalar_t<V>;
+        V acc = vzero(xs);
+        const int64_t b = __ldg(rowptr + s), e = __ldg(rowptr + s + 1);
+        if constexpr (sizeof(S) == 8) {
+            for (int64_t k = b; k < e; ++k) acc = vaxpy(__ldg(val64 + k), x[__ldg(col + k)], acc);
+        } else {
+            for (int64_t k = b; k < e; ++k) acc = vaxpy(__ldg(val32 + k), x[__ldg(col + k)], acc);
+        }
+        return acc;
+    }
+};
+
+}  // namespace msb
+
+// ----------------------------------------------------------------------------
+// Library-side operator object (host).
+// ----------------------------------------------------------------------------
+struct msb_op {
+    int kind = 0;                // 0 Hubbard, 1 CSR
+    int64_t dim = 0;
+    // Hubbard
+    msb_model model{};
+    int intermediate = 0;
+    int sec_up = 0, sec_dn = 0;  // electrons of this operator's sector
+    msb::DevBuf<int32_t> hup, hdn;
+    msb::DevBuf<uint8_t> nup, ndn;
+    msb::DevBuf<uint32_t> sup, sdn;
+    std::vector<uint32_t> host_up, host_dn;
+    msb::HubView hub{};
+    // CSR
+    msb::DevBuf<int64_t> rowptr;
+    msb::DevBuf<int32_t> col;
+    msb::DevBuf<double> val64;
+    msb::DevBuf<float> val32;
+    msb::CsrView csr{};
+    int device = 0;
+};
+
+namespace msb {
+// Host-side sector enumeration and hopping tables (basis.cu).
+std::vector<uint32_t> sector_states(int L, int n);
+// ELL hop table [W][D] with entries (target << 1) | neg, -1 empty; counts per state.
+void hop_table(int L, int n, bool periodic, const std::vector<uint32_t>& states,
+               std::vector<int32_t>& table, std::vector<uint8_t>& count, int& W);
+void validate_model(const msb_model& m);
+// y = (A + c0) x for nvec columns (operator.cu).
+void op_apply(msb_op* op, double2 c0, const void* x, void* y, int nvec, msb_precision prec,
+              cudaStream_t st);
+}  // namespace msb

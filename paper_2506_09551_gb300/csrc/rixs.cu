@@ -1,0 +1,300 @@
+// The whole RIXS map (Eqs. 1-2) and the sector maps O2 = c^dag_{j,up},
+// O1 = c_{j,up}.
+//
+// Pipeline of msb_rixs_map:
+//   1. H on (n_up, n_dn) and H' = H - Uc (n_{j,up} + n_{j,dn}) on (n_up+1, n_dn).
+//   2. |G>, E_G: FP64 Lanczos (unless the caller passes G).
+//   3. E = O2 |G>.
+//   4. One multi-shift solve (H' - E_G - i Gamma - w_seed - s_k) x_k = E with
+//      s_k = w_in[k] - w_seed: x_k = Psi(w_in[k]) (Eq. 2, App. C).  Only the
+//      components that O1 reads are carried per shift (the per-shift update is
+//      elementwise, so the others are never needed): the rows u' of the
+//      intermediate sector with site j occupied by the up electron.
+//   5. phi_k = O1 Psi_k (Eq. 1).
+//   6. Batched Lanczos continued fraction of H for every phi_k (Eq. 1).
+#include <chrono>
+#include <memory>
+#include <cmath>
+#include <vector>
+
+#include "kernels.cuh"
+#include "msbicg_impl.cuh"
+
+namespace msb {
+
+// y[dst_row, d] = sign * x[src_row, d] for every column; map entry
+// (src_row << 1) | neg, or -1 for a zero row.  Src real (double) or complex.
+template <typename VS, typename VD>
+__global__ void __launch_bounds__(256) k_rowmap(const VS* __restrict__ x, VD* __restrict__ y,
+                                                const int32_t* __restrict__ map, int64_t rows_dst, int64_t Ddn,
+                                                int64_t ld_x, int64_t ld_y) {
+    const int64_t n = rows_dst * Ddn;
+    const VS* __restrict__ xc = x + int64_t(blockIdx.y) * ld_x;
+    VD* __restrict__ yc = y + int64_t(blockIdx.y) * ld_y;
+    for (int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < n; s += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t row = s / Ddn, d = s - row * Ddn;
+        const int32_t m = __ldg(map + row);
+        VD out = vzero(VD{});
+        if (m >= 0) {
+            const VS v = xc[int64_t(m >> 1) * Ddn + d];
+            if constexpr (is_cplx_v<VS>) {
+                out = mk(scalar_t<VD>(v.x), scalar_t<VD>(v.y));
+            } else {
+                out = mk(scalar_t<VD>(v), scalar_t<VD>(0));
+            }
+            if (m & 1) out = vsub(vzero(VD{}), out);
+        }
+        yc[s] = out;
+    }
+}
+
+static std::vector<int32_t> rank_table(const std::vector<uint32_t>& st, int L) {
+    std::vector<int32_t> r(size_t(1) << L, -1);
+    for (size_t i = 0; i < st.size(); ++i) r[st[i]] = int32_t(i);
+    return r;
+}
+
+static inline int jw_sign_below(uint32_t u, int j) { return __builtin_popcount(u & ((1u << j) - 1u)) & 1; }
+
+// Row map of c^dag_{j,up}: dst rows = up states with n+1 electrons.
+static std::vector<int32_t> cdag_rowmap(int L, int n_up, int j) {
+    auto src = sector_states(L, n_up), dst = sector_states(L, n_up + 1);
+    auto rs = rank_table(src, L);
+    std::vector<int32_t> m(dst.size(), -1);
+    for (size_t r = 0; r < dst.size(); ++r) {
+        const uint32_t u = dst[r];
+        if (!((u >> j) & 1u)) continue;
+        const uint32_t v = u ^ (1u << j);
+        m[r] = (rs[v] << 1) | jw_sign_below(v, j);
+    }
+    return m;
+}
+
+// Row map of c_{j,up}: dst rows = up states with n electrons, src n+1.
+static std::vector<int32_t> c_rowmap(int L, int n_up, int j) {
+    auto dst = sector_states(L, n_up), src = sector_states(L, n_up + 1);
+    auto rs = rank_table(src, L);
+    std::vector<int32_t> m(dst.size(), -1);
+    for (size_t r = 0; r < dst.size(); ++r) {
+        const uint32_t u = dst[r];
+        if ((u >> j) & 1u) continue;
+        const uint32_t v = u | (1u << j);
+        m[r] = (rs[v] << 1) | jw_sign_below(u, j);
+    }
+    return m;
+}
+
+template <typename VS, typename VD>
+static void launch_rowmap(const VS* x, VD* y, const std::vector<int32_t>& map, int64_t Ddn, int64_t ld_x, int64_t ld_y,
+                          int nvec, cudaStream_t st, int64_t& launches) {
+    DevBuf<int32_t> dmap(map.size());
+    dmap.upload(map.data(), map.size(), st);
+    const int64_t n = int64_t(map.size()) * Ddn;
+    k_rowmap<VS, VD><<<dim3(grid_for(n, 256, 8), nvec), 256, 0, st>>>(x, y, dmap.p, int64_t(map.size()), Ddn, ld_x, ld_y);
+    MSB_LAUNCH_CHECK();
+    MSB_CUDA(cudaStreamSynchronize(st));   // dmap is freed on return
+    ++launches;
+}
+
+static void apply_sector_map(const msb_model& m, int site, bool create, const void* x, void* y, int nvec,
+                             msb_precision prec, cudaStream_t st) {
+    validate_model(m);
+    MSB_REQUIRE(site >= 0 && site < m.L, "site must be in 0..L-1");
+    MSB_REQUIRE(m.n_up + 1 <= m.L, "need n_up + 1 <= L");
+    MSB_REQUIRE(x && y && nvec >= 1 && nvec <= 65535, "invalid vectors");
+    const int64_t Ddn = int64_t(sector_states(m.L, m.n_dn).size());
+    const int64_t Dlo = int64_t(sector_states(m.L, m.n_up).size()) * Ddn;
+    const int64_t Dhi = int64_t(sector_states(m.L, m.n_up + 1).size()) * Ddn;
+    auto map = create ? cdag_rowmap(m.L, m.n_up, site) : c_rowmap(m.L, m.n_up, site);
+    const int64_t ldx = create ? Dlo : Dhi, ldy = create ? Dhi : Dlo;
+    int64_t launches = 0;
+    if (prec == MSB_FP64)
+        launch_rowmap((const double2*)x, (double2*)y, map, Ddn, ldx, ldy, nvec, st, launches);
+    else
+        launch_rowmap((const float2*)x, (float2*)y, map, Ddn, ldx, ldy, nvec, st, launches);
+}
+
+// ---------------------------------------------------------------------------
+// The map
+// ---------------------------------------------------------------------------
+void rixs_map(const msb_model& m, const msb_map_params& prm, const double* G_in, double E_G_in, const double* w_in,
+              int n_in, const double* w, int n_w, double* I_out, msb_solve_info& info, cudaStream_t st) {
+    validate_model(m);
+    MSB_REQUIRE(m.n_up + 1 <= m.L, "the intermediate sector needs n_up + 1 <= L");
+    MSB_REQUIRE(n_in >= 1 && n_in <= kMaxShifts, "n_in must be in 1..4096");
+    MSB_REQUIRE(n_w >= 1, "n_w must be >= 1");
+    MSB_REQUIRE(w_in && w && I_out, "NULL argument");
+    MSB_REQUIRE(prm.Gamma > 0 && prm.eta > 0, "Gamma and eta must be > 0");
+    MSB_REQUIRE(prm.precision == MSB_FP64 || prm.precision == MSB_FP32_MIXED, "unknown precision");
+    const auto t_start = std::chrono::steady_clock::now();
+    auto secs = [](std::chrono::steady_clock::time_point a) {
+        return std::chrono::duration<double>(std::chrono::steady_clock::now() - a).count();
+    };
+    int64_t launches = 0;
+    // operators
+    std::unique_ptr<msb_op> opH, opHp;
+    {
+        msb_op* a = nullptr;
+        msb_status s1 = msb_op_create_hubbard(&m, 0, &a);
+        if (s1 != MSB_OK) fail(s1, msb_last_error());
+        opH.reset(a);
+        s1 = msb_op_create_hubbard(&m, 1, &a);
+        if (s1 != MSB_OK) fail(s1, msb_last_error());
+        opHp.reset(a);
+    }
+    const int64_t D = opH->dim, Dp = opHp->dim, Ddn = opH->hub.Ddn;
+
+    // ground state
+    auto t0 = std::chrono::steady_clock::now();
+    DevBuf<double> gbuf;
+    const double* G = G_in;
+    double E_G = E_G_in;
+    if (!G) {
+        gbuf.alloc(D);
+        GroundResult gr;
+        ground_state(opH.get(), prm.gs_tol, prm.gs_maxit, nullptr, gbuf.p, gr, st);
+        if (gr.status != MSB_OK) fail(gr.status, "ground state: tolerance not reached");
+        G = gbuf.p;
+        E_G = gr.E;
+        info.gs_residual = gr.residual;
+        info.matvecs += gr.matvecs;
+        launches += gr.launches;
+    }
+    info.E_G = E_G;
+    info.seconds_ground_state = secs(t0);
+
+    // E = O2 |G>
+    t0 = std::chrono::steady_clock::now();
+    const size_t csz = prm.precision == MSB_FP64 ? sizeof(double2) : sizeof(float2);
+    DevBuf<char> Ebuf(size_t(Dp) * csz);
+    {
+        auto map = cdag_rowmap(m.L, m.n_up, m.core_site);
+        if (prm.precision == MSB_FP64)
+            launch_rowmap(G, (double2*)Ebuf.p, map, Ddn, D, Dp, 1, st, launches);
+        else
+            launch_rowmap(G, (float2*)Ebuf.p, map, Ddn, D, Dp, 1, st, launches);
+    }
+
+    // rows of the intermediate sector that O1 reads (site j up-occupied)
+    const auto up_hi = sector_states(m.L, m.n_up + 1);
+    std::vector<int32_t> rows;
+    std::vector<int32_t> pos(up_hi.size(), -1);
+    for (size_t r = 0; r < up_hi.size(); ++r)
+        if ((up_hi[r] >> m.core_site) & 1u) { pos[r] = int32_t(rows.size()); rows.push_back(int32_t(r)); }
+    DevBuf<int32_t> drows(rows.size());
+    drows.upload(rows.data(), rows.size(), st);
+    const int64_t n_out = int64_t(rows.size()) * Ddn;
+
+    // seed and shifts
+    int s0 = prm.seed_index;
+    if (s0 < 0) {
+        s0 = 0;
+        for (int k = 1; k < n_in; ++k) if (std::fabs(w_in[k]) < std::fabs(w_in[s0])) s0 = k;
+    }
+    MSB_REQUIRE(s0 < n_in, "seed_index out of range");
+    SolveProblem pr;
+    pr.n = Dp;
+    pr.ns = n_in;
+    pr.b = Ebuf.p;
+    pr.n_out = n_out;
+    pr.rows = drows.p;
+    pr.rowlen = Ddn;
+    pr.c0 = make_double2(-E_G - w_in[s0], -prm.Gamma);
+    pr.tol = prm.solve_tol;
+    pr.maxit = prm.maxit;
+    pr.block = pick_block(prm.block, prm.precision);
+    pr.prec = prm.precision;
+    pr.shifts.resize(n_in);
+    for (int k = 0; k < n_in; ++k) pr.shifts[k] = make_double2(w_in[k] - w_in[s0], 0.0);
+    DevBuf<char> Xsub(size_t(n_in) * n_out * csz);
+    pr.x = Xsub.p;
+    SolveResult sr;
+    multishift_solve(opHp.get(), pr, sr, st);
+    MSB_CUDA(cudaStreamSynchronize(st));
+    launches += sr.launches;
+    info.iterations = sr.iterations;
+    info.n_converged = sr.n_converged;
+    info.flushes = sr.flushes;
+    info.seed_residual = sr.seed_residual;
+    double mx = 0;
+    for (double r : sr.resid) mx = std::max(mx, r);
+    info.max_shift_residual = mx;
+    info.matvecs += sr.iterations;
+    if (sr.status != MSB_OK && sr.status != MSB_EMAXITER) fail(sr.status, "multi-shift solve failed");
+    Ebuf.release();
+
+    // phi_k = O1 Psi_k from the carried rows
+    std::vector<int32_t> omap(opH->hub.Dup, -1);
+    {
+        const auto up_lo = sector_states(m.L, m.n_up);
+        auto rhi = rank_table(up_hi, m.L);
+        for (size_t r = 0; r < up_lo.size(); ++r) {
+            const uint32_t u = up_lo[r];
+            if ((u >> m.core_site) & 1u) continue;
+            const int32_t src = pos[rhi[u | (1u << m.core_site)]];
+            omap[r] = (src << 1) | jw_sign_below(u, m.core_site);
+        }
+    }
+    DevBuf<char> Phi(size_t(n_in) * D * csz);
+    if (prm.precision == MSB_FP64)
+        launch_rowmap((const double2*)Xsub.p, (double2*)Phi.p, omap, Ddn, n_out, D, n_in, st, launches);
+    else
+        launch_rowmap((const float2*)Xsub.p, (float2*)Phi.p, omap, Ddn, n_out, D, n_in, st, launches);
+    Xsub.release();
+    drows.release();
+    info.seconds_solve = secs(t0);
+
+    // second step
+    t0 = std::chrono::steady_clock::now();
+    CFResult cr;
+    continued_fraction(opH.get(), Phi.p, n_in, E_G, w, n_w, prm.eta, prm.cf_tol, prm.cf_check, prm.cf_maxdepth,
+                       prm.precision, I_out, cr, st);
+    launches += cr.launches;
+    info.matvecs += cr.matvecs;
+    int dmax = 0, dmin = 1 << 30;
+    for (int d : cr.depth) { dmax = std::max(dmax, d); dmin = std::min(dmin, d); }
+    info.cf_depth_max = dmax;
+    info.cf_depth_min = dmin;
+    info.seconds_second_step = secs(t0);
+    info.seconds_total = secs(t_start);
+    info.kernel_launches = launches;
+    if (sr.status == MSB_EMAXITER) fail(MSB_EMAXITER, "some incident energies did not converge (map written)");
+}
+
+}  // namespace msb
+
+extern "C" msb_status msb_apply_cdag_up(const msb_model* model, int site, const void* x, void* y, int nvec,
+                                        msb_precision prec, void* stream) {
+    return msb::guard("msb_apply_cdag_up", [&] {
+        msb::require_device();
+        MSB_REQUIRE(model != nullptr, "model is NULL");
+        msb::apply_sector_map(*model, site, true, x, y, nvec, prec, (cudaStream_t)stream);
+    });
+}
+
+extern "C" msb_status msb_apply_c_up(const msb_model* model, int site, const void* x, void* y, int nvec,
+                                     msb_precision prec, void* stream) {
+    return msb::guard("msb_apply_c_up", [&] {
+        msb::require_device();
+        MSB_REQUIRE(model != nullptr, "model is NULL");
+        msb::apply_sector_map(*model, site, false, x, y, nvec, prec, (cudaStream_t)stream);
+    });
+}
+
+extern "C" msb_status msb_rixs_map(const msb_model* model, const msb_map_params* params, const double* G, double E_G,
+                                   const double* w_in, int n_in, const double* w, int n_w, double* I_out,
+                                   msb_solve_info* info, void* stream) {
+    return msb::guard("msb_rixs_map", [&] {
+        msb::require_device();
+        MSB_REQUIRE(model != nullptr && params != nullptr, "NULL argument");
+        msb::g_alloc_bytes = 0;
+        msb_solve_info local{};
+        msb::StreamScope scope((cudaStream_t)stream);
+        struct Fill {
+            msb_solve_info* dst; msb_solve_info* src;
+            ~Fill() { if (dst) { src->device_bytes = msb::g_alloc_bytes; *dst = *src; } }
+        } fill{info, &local};
+        msb::rixs_map(*model, *params, G, E_G, w_in, n_in, w, n_w, I_out, local, scope.s);
+        scope.finish();
+    });
+}

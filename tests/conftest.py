@@ -11,3 +11,20 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a) and the built library")
     config.addinivalue_line("markers", "slow: takes more than a few seconds on the CPU")
+
+
+@pytest.fixture(scope="session")
+def lib():
+    """The built C-ABI library (built in-tree on first use)."""
+    from paper_2506_09551_gb300 import build, native
+    build.build()
+    return native.load()
+
+
+@pytest.fixture(scope="session")
+def cuda(lib):
+    """A usable CUDA device with the library loaded; GPU tests fail (not skip) without it."""
+    import torch
+    assert torch.cuda.is_available(), "GPU test run without a CUDA device"
+    torch.cuda.set_device(0)
+    return torch.device("cuda:0")
