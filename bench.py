@@ -1,0 +1,393 @@
+#!/usr/bin/env python
+"""Benchmark: RIXS map throughput (incident x loss energy points per second).
+
+One step = one whole RIXS map of the workload (Eqs. 1-2): Hubbard operators,
+FP64 Lanczos ground state, the multi-shifted BiCG solve for every incident
+energy, the sector maps and the batched continued fraction of the second step.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  `value` times msb_rixs_map_ops (operators
+built beforehand, map left on the device) with CUDA events on the calling
+stream; `e2e` times msb_rixs_map (host grids in, host map out, operators
+built inside the call) with a wall clock.  Every kernel launch inside the
+timed steps is bracketed by CUDA events by the library's profiler, which
+gives the dominant kernel's achieved bandwidth / FLOP rate for `roofline`.
+Under torchrun each rank computes the map of its own core site (independent
+problems, no collective on the data path): weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads  # noqa: E402
+
+# name -> (workload, precision, solve_tol, cf_tol)
+WORKLOADS = {
+    "hubbard-L12-fp64": (workloads.CHAIN12, 0, 1e-10, 1e-10),
+    "hubbard-L14-mixed": (workloads.CHAIN14, 1, 1e-8, 1e-8),
+    "hubbard-L8-fp64": (workloads.CHAIN8, 0, 1e-10, 1e-10),
+}
+DEFAULT = "hubbard-L12-fp64"
+
+# Roofline denominators.  HBM: the measured copy bandwidth of this machine.  FP64:
+# 152 SMs x 2 FP64 FMA per clock x 2 FLOP x 2.07 GHz (nominal 1.25 TFLOP/s).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {"hbm_gbs": 6800.0, "fallback": True}
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu = gpu_id
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            lines = open(self.path).read().strip().splitlines()
+        except OSError:
+            lines = []
+        for ln in lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if self.path:
+            try:
+                os.unlink(self.path)
+            except OSError:
+                pass
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the oracle, single-threaded, on a bounded sample
+# ---------------------------------------------------------------------------
+def oracle_costs(name: str):
+    path = os.path.join(ROOT, "profiles", f"oracle_costs_{name}.json")
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except OSError:
+        return None
+
+
+def cpu_baseline_worker(name: str, n_iter: int = 20) -> dict:
+    """Runs in a fresh single-threaded process: build, ground state, and a
+    bounded number of BiCGStab iterations / continued-fraction steps of one
+    row of the map, all with the oracle's own functions.  The whole map's time
+    is scaled from these with the oracle's per-row counts for this workload."""
+    import scipy.sparse as sp
+    from oracle import hubbard, solvers, spectrum
+    wl = WORKLOADS[name][0]
+    t0 = time.perf_counter()
+    m = hubbard.RixsModel(wl.L, wl.n_up, wl.n_dn, wl.t, wl.U, wl.Uc, wl.core_site)
+    t_build = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    E_G, G, _ = solvers.ground_state(m.H, workloads.lanczos_start(m.H.shape[0], wl.lanczos_seed), kmax=300)
+    t_gs = time.perf_counter() - t0
+    k = wl.n_in // 2
+    n = m.Hp.shape[0]
+    A = (m.Hp - (E_G + wl.w_in[k] + 1j * wl.Gamma) * sp.identity(n)).tocsr()
+    b = (m.O2 @ G).astype(np.complex128)
+    t0 = time.perf_counter()
+    x, nmv = solvers.bicgstab(lambda v: A @ v, b, 1e-13, maxit=n_iter, restarts=1, strict=False)
+    t_solve = time.perf_counter() - t0
+    lz = spectrum._Lanczos(m.H, m.O1 @ x)
+    t0 = time.perf_counter()
+    lz.advance(n_iter)
+    t_cf = time.perf_counter() - t0
+    costs = oracle_costs(name)
+    per_mv = t_solve / max(nmv, 1)
+    per_step = t_cf / max(len(lz.a), 1)
+    if costs:
+        mv_row, depth_row = costs["mean_solve_matvecs"], costs["mean_cf_depth"]
+        src = f"per-row counts from profiles/oracle_costs_{name}.json ({len(costs['rows'])} rows run in full)"
+    else:
+        mv_row, depth_row = float("nan"), float("nan")
+        src = "no recorded per-row counts"
+    T_map = t_build + t_gs + wl.n_in * (mv_row * per_mv + depth_row * per_step)
+    pts = wl.n_in * wl.n_w
+    return {
+        "value": pts / T_map, "unit": "map points/s", "cores": 1, "kind": "oracle",
+        "sample": (f"oracle (numpy/scipy, 1 thread) on {name}: build H,H' ({t_build:.1f}s), Lanczos ground state "
+                   f"({t_gs:.1f}s), {nmv} BiCGStab MVMs and {len(lz.a)} CF Lanczos steps of row {k} "
+                   f"({t_solve + t_cf:.1f}s); whole map = build + ground state + {wl.n_in} rows x "
+                   f"({mv_row:.0f} MVMs + {depth_row:.0f} CF steps), {src}"),
+        "seconds_measured": t_build + t_gs + t_solve + t_cf,
+        "map_seconds_scaled": T_map,
+    }
+
+
+def run_cpu_baseline(name: str) -> dict:
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-baseline-worker", "--workload", name],
+                       capture_output=True, text=True, env=env, timeout=900)
+    for ln in r.stdout.splitlines()[::-1]:
+        if ln.startswith("{"):
+            return json.loads(ln)
+    return {"value": None, "unit": "map points/s", "cores": 1, "kind": "oracle",
+            "sample": "failed: " + (r.stderr.strip().splitlines() or ["?"])[-1]}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def dominant_roofline(stats, prec, peaks):
+    top = max(stats, key=lambda s: s["ms"])
+    avg_ms = top["ms"] / top["launches"]
+    if prec == 0:
+        achieved = top["alg_flops"] / top["launches"] / (avg_ms * 1e-3) / 1e12
+        return top, {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "kernel": top["name"],
+                     "peak_source": "derived FP64: 152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz"}
+    achieved = top["alg_bytes"] / top["launches"] / (avg_ms * 1e-3) / 1e9
+    return top, {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                 "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": top["name"],
+                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}
+
+
+def gpu_arm(args, rank, world):
+    import torch
+    from paper_2506_09551_gb300 import api, native
+
+    native.load()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    wl, prec, stol, ctol = WORKLOADS[args.workload]
+    core = rank % wl.L
+    m = api.model(wl.L, wl.n_up, wl.n_dn, wl.t, wl.U, wl.Uc, core_site=core)
+    p = api.map_params(Gamma=wl.Gamma, eta=wl.eta, gs_tol=wl.gs_tol, solve_tol=stol, cf_tol=ctol, precision=prec)
+    H = api.Operator.hubbard(m, False)
+    Hp = api.Operator.hubbard(m, True)
+    w_in, w = wl.w_in, wl.w
+    out = torch.empty((len(w_in), len(w)), dtype=torch.float64, device="cuda")
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    lib = native.load()
+    for _ in range(args.warmup):
+        api.rixs_map_ops(H, Hp, p, w_in, w, out=out)
+    torch.cuda.synchronize()
+    barrier()
+    lib.msb_profile_reset()
+    lib.msb_profile_enable(1)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    infos = []
+    gpu_id = str(local)
+    try:
+        u = torch.cuda.get_device_properties(local).uuid
+        gpu_id = "GPU-" + str(u) if not str(u).startswith("GPU-") else str(u)
+    except Exception:
+        pass
+    with ClockSampler(gpu_id) as clk:
+        torch.cuda.synchronize()
+        barrier()
+        e0.record(stream)
+        for _ in range(args.steps):
+            _, info, st = api.rixs_map_ops(H, Hp, p, w_in, w, out=out)
+            infos.append(info)
+        e1.record(stream)
+        e1.synchronize()
+        torch.cuda.synchronize()
+        barrier()
+    lib.msb_profile_enable(0)
+    stats = native.profile_read()
+    ms = e0.elapsed_time(e1) / args.steps
+    clocks = clk.summary()
+    # whole-job time = max over ranks
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    pts = len(w_in) * len(w)
+    value = world * pts / (ms * 1e-3)
+
+    print(f"[bench] {args.workload}: {ms:.1f} ms per map over {args.steps} steps", file=sys.stderr, flush=True)
+    # end to end through the public host API (operators built, grids in, map out)
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    if args.no_e2e:
+        I_host = out.cpu().numpy()
+    else:
+        I_host, info_e2e, _ = api.rixs_map(m, p, w_in, w)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    I_dev = out.cpu().numpy()
+    same = float(np.max(np.abs(I_dev - I_host)) / np.max(np.abs(I_host)))
+
+    peaks = measured_peaks()
+    top, roof = dominant_roofline(stats, prec, peaks)
+    total_ms = sum(s["ms"] for s in stats)
+    apply_cls = [s for s in stats if s["name"] in ("cf_apply", "seed_mvm", "h_apply")]
+    h_gbs = (sum(s["alg_bytes"] for s in apply_cls) / (sum(s["ms"] for s in apply_cls) * 1e-3) / 1e9
+             if apply_cls else None)
+    launches = int(sum(i["kernel_launches"] for i in infos) / args.steps)
+    line = {
+        "metric": "RIXS map (w_in, w) points/s",
+        "value": value,
+        "unit": "map points/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "c128" if prec == 0 else "c64 vectors, f64 scalars",
+        "data": "synthetic: 1D Hubbard ring, random-start Lanczos ground state",
+        "config": {"workload": args.workload, "L": wl.L, "n_up": wl.n_up, "n_dn": wl.n_dn,
+                   "dim_ground": int(H.dim), "dim_intermediate": int(Hp.dim), "n_w_in": wl.n_in, "n_w": wl.n_w,
+                   "Gamma": wl.Gamma, "eta": wl.eta, "solve_tol": stol, "cf_tol": ctol,
+                   "precision": "FP64" if prec == 0 else "FP32-mixed",
+                   "parallelism": f"{world} independent maps (core site = rank)",
+                   "l2": "working set (vectors of GBs) larger than L2; no flush needed"},
+        "e2e": {"value": world * pts / e2e_s, "unit": "map points/s",
+                "h2d_bytes_per_step": int(8 * (len(w_in) + len(w))) + 2 * 8 * 4,
+                "d2h_bytes_per_step": int(8 * pts), "seconds": e2e_s,
+                "max_rel_diff_vs_value_map": same},
+        "gpu_launches": launches,
+        "roofline": roof,
+        "h_apply_alg_gbs": h_gbs,
+        "clocks": clocks,
+        "solve": {k: infos[-1][k] for k in ("iterations", "n_converged", "matvecs", "cf_depth_max",
+                                            "cf_depth_min", "seconds_ground_state", "seconds_solve",
+                                            "seconds_second_step", "device_bytes", "E_G")},
+        "kernels": sorted([{"name": s["name"], "launches": s["launches"], "ms": round(s["ms"], 3),
+                            "share": round(s["ms"] / total_ms, 4)} for s in stats],
+                          key=lambda d: -d["ms"]),
+    }
+    return line
+
+
+def reference_arm(args) -> dict:
+    """The oracle on the host cores: each step is a bounded sample of the same
+    workload (see cpu_baseline_worker), scaled to a whole map."""
+    wl, prec, stol, ctol = WORKLOADS[args.workload]
+    vals = []
+    for i in range(args.warmup + args.steps):
+        r = run_cpu_baseline(args.workload)
+        if i >= args.warmup:
+            vals.append(r)
+    v = statistics.mean([r["value"] for r in vals if r["value"]]) if any(r["value"] for r in vals) else None
+    ms = wl.n_in * wl.n_w / v * 1e3 if v else None
+    cb = dict(vals[-1])
+    cb["value"] = v
+    return {"metric": "RIXS map (w_in, w) points/s", "value": v, "unit": "map points/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+            "impl": "reference", "config": {"workload": args.workload},
+            "cpu_baseline": cb, "e2e": {"value": v, "unit": "map points/s", "h2d_bytes_per_step": 0,
+                                        "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end map (profiling runs)")
+    ap.add_argument("--cpu-baseline-worker", action="store_true", help=argparse.SUPPRESS)
+    args = ap.parse_args()
+
+    if args.cpu_baseline_worker:
+        print(json.dumps(cpu_baseline_worker(args.workload)))
+        return
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(reference_arm(args)), flush=True)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl")
+    line = gpu_arm(args, rank, world)
+    if rank == 0:
+        if not args.no_cpu_baseline and world == 1:
+            line["cpu_baseline"] = run_cpu_baseline(args.workload)
+        elif not args.no_cpu_baseline:
+            line["cpu_baseline"] = None
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -249,6 +249,45 @@ msb_status msb_rixs_map(const msb_model *model, const msb_map_params *params,
                         const double *w, int n_w, double *I_out, msb_solve_info *info,
                         void *stream);
 
+/* ------------------------------------------------------------------------ */
+/* Kernel profiling                                                          */
+/* ------------------------------------------------------------------------ */
+
+/* Per kernel class: launches, summed CUDA-event durations (each launch is
+ * bracketed by events on the stream it runs on), and the algorithmic DRAM
+ * bytes and floating-point operations of those launches (what the method
+ * must move / compute for the sizes involved: each vector read or written
+ * once per use, hop tables and scalars not counted). */
+typedef struct {
+    char name[48];
+    int64_t launches;
+    double ms;
+    double alg_bytes;
+    double alg_flops;
+} msb_kernel_stat;
+
+/* Turn profiling on or off for the whole process.  While on, the solver
+ * launches its kernels directly instead of replaying CUDA graphs, so every
+ * launch can be timed; the arithmetic is unchanged. */
+void msb_profile_enable(int on);
+
+/* Forget all collected statistics. */
+void msb_profile_reset(void);
+
+/* Copy up to `max` kernel classes with at least one launch into `out` (HOST
+ * array; may be NULL to count) and return how many there are. */
+int msb_profile_read(msb_kernel_stat *out, int max);
+
+/* Same map with the operators already built and the result left on the
+ * device: H = msb_op_create_hubbard(model, 0), Hp = msb_op_create_hubbard(model,
+ * 1) of one model (checked); w_in, w are HOST grids (copied in); I_dev is a
+ * DEVICE output of n_in * n_w doubles.  For repeated maps of one model, and to
+ * time the path with its inputs resident in device memory.
+ * Synchronises `stream`. */
+msb_status msb_rixs_map_ops(msb_op *H, msb_op *Hp, const msb_map_params *params, const double *G,
+                            double E_G, const double *w_in, int n_in, const double *w, int n_w,
+                            double *I_dev, msb_solve_info *info, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

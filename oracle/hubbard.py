@@ -81,8 +81,11 @@ class Sector:
         self.d = np.tile(self.dn, self.D_up)
         # full Jordan-Wigner occupation string of each basis state
         self.jw = self._to_jw(self.u, self.d)
-        self._sorted = np.argsort(self.jw, kind="stable")
-        self._jw_sorted = self.jw[self._sorted]
+        # rank of every L-bit string within its species' sector (-1 if outside)
+        self._rank_up = np.full(1 << self.L, -1, dtype=np.int64)
+        self._rank_up[self.up] = np.arange(self.D_up)
+        self._rank_dn = np.full(1 << self.L, -1, dtype=np.int64)
+        self._rank_dn[self.dn] = np.arange(self.D_dn)
 
     def _to_jw(self, u: np.ndarray, d: np.ndarray) -> np.ndarray:
         out = np.zeros_like(u)
@@ -91,13 +94,21 @@ class Sector:
             out |= ((d >> i) & 1) << orbital(self.L, i, 1, self.order)
         return out
 
+    def _from_jw(self, jw: np.ndarray):
+        u = np.zeros_like(jw)
+        d = np.zeros_like(jw)
+        for i in range(self.L):
+            u |= ((jw >> orbital(self.L, i, 0, self.order)) & 1) << i
+            d |= ((jw >> orbital(self.L, i, 1, self.order)) & 1) << i
+        return u, d
+
     def index_of_jw(self, jw: np.ndarray) -> np.ndarray:
-        """Basis index of each JW string (every string must lie in the sector)."""
-        pos = np.searchsorted(self._jw_sorted, jw)
-        pos = np.minimum(pos, self.dim - 1)
-        if not np.all(self._jw_sorted[pos] == jw):
+        """Basis index rank(u) * D_dn + rank(d) of each JW string (must lie in the sector)."""
+        u, d = self._from_jw(jw)
+        iu, idn = self._rank_up[u], self._rank_dn[d]
+        if np.any(iu < 0) or np.any(idn < 0):
             raise ValueError("state outside sector")
-        return self._sorted[pos]
+        return iu * self.D_dn + idn
 
     def occupation(self, site: int, spin: int) -> np.ndarray:
         occ = self.u if spin == 0 else self.d

@@ -170,6 +170,21 @@ def apply_c_up(m: N.msb_model, site: int, x: torch.Tensor, out_dim: int, prec: i
     return y
 
 
+def rixs_map_ops(H: Operator, Hp: Operator, params: N.msb_map_params, w_in, w, G: torch.Tensor | None = None,
+                 E_G: float = 0.0, out: torch.Tensor | None = None, allow_status=(N.MSB_EMAXITER,)):
+    """Map from prebuilt operators into a device tensor (n_in, n_w) float64."""
+    w_in = np.ascontiguousarray(w_in, dtype=np.float64)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    I = out if out is not None else torch.empty((len(w_in), len(w)), dtype=torch.float64, device="cuda")
+    info = N.msb_solve_info()
+    st = N.load().msb_rixs_map_ops(H.h, Hp.h, C.byref(params), _ptr(G) if G is not None else None, E_G,
+                                   w_in.ctypes.data_as(C.POINTER(C.c_double)), len(w_in),
+                                   w.ctypes.data_as(C.POINTER(C.c_double)), len(w), _ptr(I), C.byref(info),
+                                   _stream())
+    N.check(st, allow=allow_status)
+    return I, info.as_dict(), st
+
+
 def rixs_map(m: N.msb_model, params: N.msb_map_params, w_in, w, G: torch.Tensor | None = None, E_G: float = 0.0,
              allow_status=(N.MSB_EMAXITER,)):
     """The RIXS map I[n_in, n_w] (numpy), the solve info (dict) and the status."""

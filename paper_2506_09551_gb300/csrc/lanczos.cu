@@ -12,6 +12,7 @@
 
 #include "kernels.cuh"
 #include "msbicg_impl.cuh"
+#include "profile.cuh"
 
 namespace msb {
 
@@ -269,8 +270,10 @@ __global__ void k_scale_real(double* g, int64_t n, double f) {
 // Ground state
 // ---------------------------------------------------------------------------
 template <class View>
-static void ground_state_impl(const View& view, int64_t n, double tol, int maxit, const double* start, double* g,
-                              GroundResult& out, cudaStream_t st) {
+static void ground_state_impl(const msb_op* op, const View& view, int64_t n, double tol, int maxit, const double* start,
+                              double* g, GroundResult& out, cudaStream_t st) {
+    const double vb = 8.0 * double(n);                       // one real FP64 vector
+    const double hxf = 0.5 * op->hx_flops() + op->matrix_bytes(8) * 0.0;
     const int grid = grid_for(n, 256, 8);
     DevBuf<double> Q(3 * size_t(n)), part(size_t(grid) * 3), a_dev(maxit + 1), b_dev(maxit + 1), bcur(1), hbuf(n);
     DevBuf<int> col0(1);
@@ -297,11 +300,20 @@ static void ground_state_impl(const View& view, int64_t n, double tol, int maxit
         for (; k < kmax; ++k) {
             if (accumulate) { k_axpy_real<<<grid, 256, 0, st>>>(g, q, n, y[k]); ++out.launches; }
             if (accumulate && k == kmax - 1) break;
-            k_lz_apply<View, double><<<dim3(grid, 1), 256, 0, st>>>(view, q, qp, w, n, col0.p, bcur.p, part.p);
-            k_lz_sum<<<1, 256, 0, st>>>(part.p, grid, col0.p, a_dev.p, 1, k);
-            k_lz_orth<double><<<dim3(grid, 1), 256, 0, st>>>(q, w, n, col0.p, a_dev.p + k, part.p);
-            k_lz_norm<<<1, 256, 0, st>>>(part.p, grid, col0.p, b_dev.p, 1, k, bcur.p);
-            k_lz_scale<double><<<dim3(grid, 1), 256, 0, st>>>(w, n, col0.p, bcur.p);
+            {
+                ProfScope ps("ground_state", st, 3 * vb + op->matrix_bytes(8), hxf + 4.0 * n);
+                k_lz_apply<View, double><<<dim3(grid, 1), 256, 0, st>>>(view, q, qp, w, n, col0.p, bcur.p, part.p);
+            }
+            { ProfScope ps("ground_state", st, 0, 0); k_lz_sum<<<1, 256, 0, st>>>(part.p, grid, col0.p, a_dev.p, 1, k); }
+            {
+                ProfScope ps("ground_state", st, 3 * vb, 4.0 * n);
+                k_lz_orth<double><<<dim3(grid, 1), 256, 0, st>>>(q, w, n, col0.p, a_dev.p + k, part.p);
+            }
+            { ProfScope ps("ground_state", st, 0, 0); k_lz_norm<<<1, 256, 0, st>>>(part.p, grid, col0.p, b_dev.p, 1, k, bcur.p); }
+            {
+                ProfScope ps("ground_state", st, 2 * vb, 1.0 * n);
+                k_lz_scale<double><<<dim3(grid, 1), 256, 0, st>>>(w, n, col0.p, bcur.p);
+            }
             out.launches += 5;
             ++out.matvecs;
             MSB_LAUNCH_CHECK();
@@ -364,8 +376,9 @@ void ground_state(msb_op* H, double tol, int maxit, const double* start, double*
     MSB_REQUIRE(H != nullptr && g != nullptr, "NULL argument");
     MSB_REQUIRE(maxit >= 2, "maxit must be >= 2");
     MSB_REQUIRE(tol > 0, "tol must be > 0");
-    if (H->kind == 0) ground_state_impl(H->hub, H->dim, tol, maxit, start, g, out, st);
-    else ground_state_impl(H->csr, H->dim, tol, maxit, start, g, out, st);
+    if (H->kind == 0) ground_state_impl(H, H->hub, H->dim, tol, maxit, start, g, out, st);
+    else ground_state_impl(H, H->csr, H->dim, tol, maxit, start, g, out, st);
+    prof_collect();
 }
 
 // ---------------------------------------------------------------------------
@@ -415,9 +428,10 @@ __global__ void k_cf_eval(const double* __restrict__ a, const double* __restrict
 }
 
 template <class View, typename V>
-static void cf_impl(const View& view, int64_t n, const void* phi_v, int nv, double E0, const double* w, int n_w,
-                    double eta, double cf_tol, int check, int maxdepth, double* I_out, CFResult& out,
-                    cudaStream_t st) {
+static void cf_impl(const msb_op* op, const View& view, int64_t n, const void* phi_v, int nv, double E0, const double* w,
+                    int n_w, double eta, double cf_tol, int check, int maxdepth, double* I_out, CFResult& out,
+                    cudaStream_t st, bool I_dev) {
+    const double vb = double(sizeof(V)) * double(n);        // one complex vector
     const V* phi = (const V*)phi_v;
     const int grid = grid_for(n, 256, 4);
     DevBuf<V> Q(3 * size_t(nv) * n);
@@ -452,11 +466,21 @@ static void cf_impl(const View& view, int64_t n, const void* phi_v, int nv, doub
     int k = 0;
     while (nact > 0 && k < maxdepth) {
         const dim3 g2(grid, nact);
-        k_lz_apply<View, V><<<g2, 256, 0, st>>>(view, q, qp, wv, n, cols.p, bcur.p, part.p);
-        k_lz_sum<<<nact, 256, 0, st>>>(part.p, grid, cols.p, a.p, nv, k);
-        k_lz_orth<V><<<g2, 256, 0, st>>>(q, wv, n, cols.p, a.p + int64_t(k) * nv, part.p);
-        k_lz_norm<<<nact, 256, 0, st>>>(part.p, grid, cols.p, b.p, nv, k, bcur.p);
-        k_lz_scale<V><<<g2, 256, 0, st>>>(wv, n, cols.p, bcur.p);
+        {
+            ProfScope ps("cf_apply", st, nact * (3 * vb + op->matrix_bytes(sizeof(V))),
+                         nact * (op->hx_flops() + 8.0 * n));
+            k_lz_apply<View, V><<<g2, 256, 0, st>>>(view, q, qp, wv, n, cols.p, bcur.p, part.p);
+        }
+        { ProfScope ps("cf_reduce", st, 0, 0); k_lz_sum<<<nact, 256, 0, st>>>(part.p, grid, cols.p, a.p, nv, k); }
+        {
+            ProfScope ps("cf_orth", st, nact * 3 * vb, nact * 8.0 * n);
+            k_lz_orth<V><<<g2, 256, 0, st>>>(q, wv, n, cols.p, a.p + int64_t(k) * nv, part.p);
+        }
+        { ProfScope ps("cf_reduce", st, 0, 0); k_lz_norm<<<nact, 256, 0, st>>>(part.p, grid, cols.p, b.p, nv, k, bcur.p); }
+        {
+            ProfScope ps("cf_scale", st, nact * 2 * vb, nact * 2.0 * n);
+            k_lz_scale<V><<<g2, 256, 0, st>>>(wv, n, cols.p, bcur.p);
+        }
         out.launches += 5;
         out.matvecs += nact;
         MSB_LAUNCH_CHECK();
@@ -469,7 +493,11 @@ static void cf_impl(const View& view, int64_t n, const void* phi_v, int nv, doub
                                      cudaMemcpyDeviceToHost, st));
             for (int i = 0; i < nact; ++i) hdepth[hcols[i]] = k;
             depth.upload(hdepth.data(), nv, st);
-            k_cf_eval<<<nact, 128, 0, st>>>(a.p, b.p, nv, n0.p, cols.p, depth.p, E0, wdev.p, n_w, eta, I.p, diff.p);
+            {
+                ProfScope ps("cf_eval", st, 0, 20.0 * nact * n_w * double(k));
+                k_cf_eval<<<nact, 128, 0, st>>>(a.p, b.p, nv, n0.p, cols.p, depth.p, E0, wdev.p, n_w, eta, I.p,
+                                                diff.p);
+            }
             ++out.launches;
             MSB_CUDA(cudaMemcpyAsync(hdiff.data(), diff.p, 2 * nv * sizeof(double), cudaMemcpyDeviceToHost, st));
             MSB_CUDA(cudaStreamSynchronize(st));
@@ -488,26 +516,28 @@ static void cf_impl(const View& view, int64_t n, const void* phi_v, int nv, doub
     // Krylov exhaustion is detected through a tiny b: a zero tail then ends the
     // fraction exactly, which the depth rule above already covers.
     (void)scale;
-    MSB_CUDA(cudaMemcpyAsync(I_out, I.p, size_t(nv) * n_w * sizeof(double), cudaMemcpyDeviceToHost, st));
+    MSB_CUDA(cudaMemcpyAsync(I_out, I.p, size_t(nv) * n_w * sizeof(double),
+                             I_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
     MSB_CUDA(cudaStreamSynchronize(st));
     out.depth = hdepth;
 }
 
 void continued_fraction(msb_op* H, const void* phi, int n_vec, double E0, const double* w, int n_w, double eta,
                         double cf_tol, int cf_check, int cf_maxdepth, msb_precision prec, double* I_out,
-                        CFResult& out, cudaStream_t st) {
+                        CFResult& out, cudaStream_t st, bool I_dev) {
     MSB_REQUIRE(H != nullptr && phi != nullptr && w != nullptr && I_out != nullptr, "NULL argument");
     MSB_REQUIRE(n_vec >= 1 && n_vec <= 65535, "n_vec must be in 1..65535");
     MSB_REQUIRE(n_w >= 1, "n_w must be >= 1");
     MSB_REQUIRE(eta > 0, "eta must be > 0");
     MSB_REQUIRE(cf_check >= 1 && cf_maxdepth >= cf_check, "need 1 <= cf_check <= cf_maxdepth");
     if (prec == MSB_FP64) {
-        if (H->kind == 0) cf_impl<HubView, double2>(H->hub, H->dim, phi, n_vec, E0, w, n_w, eta, cf_tol, cf_check, cf_maxdepth, I_out, out, st);
-        else cf_impl<CsrView, double2>(H->csr, H->dim, phi, n_vec, E0, w, n_w, eta, cf_tol, cf_check, cf_maxdepth, I_out, out, st);
+        if (H->kind == 0) cf_impl<HubView, double2>(H, H->hub, H->dim, phi, n_vec, E0, w, n_w, eta, cf_tol, cf_check, cf_maxdepth, I_out, out, st, I_dev);
+        else cf_impl<CsrView, double2>(H, H->csr, H->dim, phi, n_vec, E0, w, n_w, eta, cf_tol, cf_check, cf_maxdepth, I_out, out, st, I_dev);
     } else {
-        if (H->kind == 0) cf_impl<HubView, float2>(H->hub, H->dim, phi, n_vec, E0, w, n_w, eta, cf_tol, cf_check, cf_maxdepth, I_out, out, st);
-        else cf_impl<CsrView, float2>(H->csr, H->dim, phi, n_vec, E0, w, n_w, eta, cf_tol, cf_check, cf_maxdepth, I_out, out, st);
+        if (H->kind == 0) cf_impl<HubView, float2>(H, H->hub, H->dim, phi, n_vec, E0, w, n_w, eta, cf_tol, cf_check, cf_maxdepth, I_out, out, st, I_dev);
+        else cf_impl<CsrView, float2>(H, H->csr, H->dim, phi, n_vec, E0, w, n_w, eta, cf_tol, cf_check, cf_maxdepth, I_out, out, st, I_dev);
     }
+    prof_collect();
 }
 
 }  // namespace msb

@@ -27,12 +27,23 @@
 // x^k over those B iterations in registers: one read and one write of each
 // per-shift vector per B iterations instead of per iteration.  The arithmetic
 // and its order are exactly those of the per-iteration update.
+//
+// Exponent management.  The seed residual of a well-placed seed falls far
+// faster than the residuals of distant shifts (1e-160 after ~1000 iterations
+// at L = 8), so r_m and zeta^k_m leave the FP32 range long before the shifts
+// converge, and the FP64 range on long runs.  Everything is linear, so the
+// seed vectors r, p, v are stored as S_m times their true values and each
+// shift's (zeta_m, zeta_{m-1}) as g_k times theirs, with S_m and g_k powers of
+// two (exact scaling: no rounding changes).  Only the scalars see the scales:
+//   gamma~ = gamma * S_m / S_{m-1},   c~ = c / S_m = alpha 2^{E_k} / zeta~_{m+1},
+//   ||r^k_m|| = ||r~_m|| 2^{E_k} / |zeta~_m|,      E_k = log2(g_k / S_m).
 #include <chrono>
 #include <cmath>
 #include <memory>
 
 #include "kernels.cuh"
 #include "msbicg_impl.cuh"
+#include "profile.cuh"
 
 namespace msb {
 
@@ -57,6 +68,9 @@ struct SeedState {
     int status;           // msb_status of the recurrence
     int maxit;
     int nactive;
+    int fexp;             // r~_m, p~_m were rescaled by 2^fexp after r_m was formed
+    int sexp;             // log2 S_m (for reporting the true seed residual)
+    int flush_J, flush_cnt, flush_first;   // work of the last fused update (profiling)
 };
 
 // ---------------------------------------------------------------------------
@@ -112,6 +126,7 @@ __global__ void __launch_bounds__(kScalarThreads) k_scalar_a(SeedState* st, cons
     const double2 beta = st->beta;
     const double2 ab_over = cdiv(cmul(alpha, beta), st->alpha_prev);   // alpha_m beta_m / alpha_{m-1}
     const int j = st->j;
+    const int fexp = st->fexp;
     for (int k = threadIdx.x; k < ns; k += blockDim.x) {
         if (!sh.active[k]) continue;
         const double2 z = sh.zeta[k], zp = sh.zeta_prev[k], s = sh.shift[k];
@@ -124,16 +139,25 @@ __global__ void __launch_bounds__(kScalarThreads) k_scalar_a(SeedState* st, cons
             sh.broken[k] = 1;
             continue;
         }
-        const double2 gamma = cdiv(cmul(beta, zp), z);    // beta_m zeta_{m-1} / zeta_m
-        const double2 c = cdiv(alpha, zn);                 // alpha_m / zeta_{m+1}
+        // beta_m zeta_{m-1} / zeta_m, times S_m / S_{m-1}
+        double2 gamma = cdiv(cmul(beta, zp), z);
+        gamma = make_double2(ldexp(gamma.x, fexp), ldexp(gamma.y, fexp));
+        // alpha_m / zeta_{m+1} / S_m
+        double2 c = cdiv(alpha, zn);
+        c = make_double2(ldexp(c.x, sh.zexp[k]), ldexp(c.y, sh.zexp[k]));
         const int64_t o = int64_t(k) * B + j;
         sh.coef64[2 * o] = gamma;
         sh.coef64[2 * o + 1] = c;
         reinterpret_cast<C*>(sh.coefv)[2 * o] = from_d2<C>(gamma);
         reinterpret_cast<C*>(sh.coefv)[2 * o + 1] = from_d2<C>(c);
         sh.nblk[k] = j + 1;
-        sh.zeta_prev[k] = z;
-        sh.zeta[k] = zn;
+        // keep zeta~ near 1: rescale the pair (zeta_{m+1}, zeta_m) by 2^q
+        const double mag = fmax(fabs(zn.x), fabs(zn.y));
+        int q = 0;
+        if (mag < 0x1p-30 || mag > 0x1p30) q = -ilogb(mag);
+        sh.zeta_prev[k] = make_double2(ldexp(z.x, q), ldexp(z.y, q));
+        sh.zeta[k] = make_double2(ldexp(zn.x, q), ldexp(zn.y, q));
+        sh.zexp[k] += q;
     }
 }
 
@@ -158,35 +182,42 @@ __global__ void __launch_bounds__(256) k_seed_update(V* ring, const V* __restric
     store_partials<3>(acc, sm, part);
 }
 
-// beta, convergence of every shift, iteration bookkeeping.
+// beta, convergence of every shift, iteration bookkeeping, seed rescaling.
 __global__ void __launch_bounds__(kScalarThreads) k_scalar_b(SeedState* st, const double* part, int nblk,
                                                              ShiftArrays sh, int ns, int nslot) {
     if (st->done) return;
     __shared__ double sm[3 * 32];
-    __shared__ double s_rnorm;
-    __shared__ int s_m, s_stop;
+    __shared__ double s_rn;      // ||r~_{m+1}|| (stored scale S_m)
+    __shared__ int s_m, s_stop, s_f;
     double v[3];
     reduce_partials<3>(part, nblk, v, sm);
     if (threadIdx.x == 0) {
         const double2 rho_new = make_double2(v[0], v[1]);
-        const double rnorm = sqrt(v[2]);
+        const double rn = sqrt(v[2]);
         st->slot = (st->slot + 1) % nslot;
         st->m += 1;
         st->j += 1;
-        st->rnorm = rnorm;
         st->alpha_prev = st->alpha;
         s_stop = 0;
-        if (!cfinite(rho_new) || !isfinite(rnorm)) {
+        int f = 0;
+        if (!cfinite(rho_new) || !isfinite(rn)) {
             st->status = MSB_ENONFINITE; s_stop = 1;
-        } else if (rnorm == 0.0) {
+        } else if (rn == 0.0) {
             st->beta = make_double2(0.0, 0.0);        // exact solution: every shift converged
         } else if (rho_new.x == 0.0 && rho_new.y == 0.0) {
             st->status = MSB_EBREAKDOWN; s_stop = 1;   // (r, r) = 0 with r != 0
         } else {
             st->beta = cdiv(rho_new, st->rho);
+            // bring ||r~|| back near ||b|| once it drifts by more than 2^20
+            const double ratio = rn / st->bnorm;
+            if (ratio < 0x1p-20 || ratio > 0x1p20) f = -ilogb(ratio);
         }
-        st->rho = rho_new;
-        s_rnorm = rnorm;
+        st->rho = make_double2(ldexp(rho_new.x, 2 * f), ldexp(rho_new.y, 2 * f));
+        st->rnorm = ldexp(rn, -st->sexp);
+        st->fexp = f;
+        st->sexp += f;
+        s_rn = rn;
+        s_f = f;
         s_m = st->m;
     }
     __syncthreads();
@@ -194,9 +225,11 @@ __global__ void __launch_bounds__(kScalarThreads) k_scalar_b(SeedState* st, cons
     int still = 0;
     for (int k = threadIdx.x; k < ns; k += blockDim.x) {
         if (!sh.active[k]) continue;
-        const double rk = s_rnorm / cabs(sh.zeta[k]);
+        // ||r^k_{m+1}|| = ||r~_{m+1}|| 2^{E_k} / |zeta~_{m+1}|
+        const double rk = ldexp(s_rn / cabs(sh.zeta[k]), sh.zexp[k]);
         sh.iters[k] = s_m;
         sh.resid[k] = rk / st->bnorm;
+        sh.zexp[k] -= s_f;       // S_{m+1} = S_m 2^f
         if (rk <= thr) { sh.active[k] = 0; sh.conv[k] = 1; }
         else ++still;
     }
@@ -208,16 +241,27 @@ __global__ void __launch_bounds__(kScalarThreads) k_scalar_b(SeedState* st, cons
     }
 }
 
-// p = r_{m+1} + beta p
+// p = 2^f (r_{m+1} + beta p), r_{m+1} <- 2^f r_{m+1} (exact power-of-two rescale)
 template <typename V>
-__global__ void __launch_bounds__(256) k_update_p(const V* ring, V* __restrict__ p, int64_t n,
+__global__ void __launch_bounds__(256) k_update_p(V* ring, V* __restrict__ p, int64_t n,
                                                   const SeedState* __restrict__ st) {
     if (st->done) return;
-    const V* __restrict__ r = ring + int64_t(st->slot) * n;
+    V* __restrict__ r = ring + int64_t(st->slot) * n;
     const double2 b = st->beta;
-    for (int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < n;
-         s += int64_t(gridDim.x) * blockDim.x)
-        p[s] = vadd(r[s], cscale(b.x, b.y, p[s]));
+    const int f = st->fexp;
+    if (f == 0) {
+        for (int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < n;
+             s += int64_t(gridDim.x) * blockDim.x)
+            p[s] = vadd(r[s], cscale(b.x, b.y, p[s]));
+    } else {
+        const double sc = ldexp(1.0, f);
+        for (int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < n;
+             s += int64_t(gridDim.x) * blockDim.x) {
+            const V rs = r[s];
+            p[s] = cscale(sc, 0.0, vadd(rs, cscale(b.x, b.y, p[s])));
+            r[s] = cscale(sc, 0.0, rs);
+        }
+    }
 }
 
 // Start of a block of iterations: nothing pending for any shift.
@@ -238,7 +282,7 @@ template <typename V, int BMAX>
 __global__ void __launch_bounds__(256) k_flush(const V* __restrict__ ring, int nslot, int64_t n_seed,
                                                V* __restrict__ P, V* __restrict__ X, int64_t n_out,
                                                const int32_t* __restrict__ rows, int64_t rowlen,
-                                               ShiftArrays sh, int ns, const SeedState* __restrict__ st) {
+                                               ShiftArrays sh, int ns, SeedState* __restrict__ st) {
     __shared__ int s_list[kMaxShifts];
     __shared__ int s_cnt;
     const int m0 = st->m0;
@@ -248,6 +292,11 @@ __global__ void __launch_bounds__(256) k_flush(const V* __restrict__ ring, int n
         for (int k = 0; k < ns; ++k)
             if (sh.nblk[k] > 0) s_list[c++] = k;
         s_cnt = c;
+        if (blockIdx.x == 0) {
+            st->flush_J = st->j;
+            st->flush_cnt = c;
+            st->flush_first = m0 == 0;
+        }
     }
     __syncthreads();
     const int cnt = s_cnt;
@@ -330,6 +379,8 @@ __global__ void __launch_bounds__(kScalarThreads) k_init_state(SeedState* st, co
         st->done = (bn == 0.0 || maxit <= 0) ? 1 : 0;
         if (bn != 0.0 && st->rho.x == 0.0 && st->rho.y == 0.0) { st->status = MSB_EBREAKDOWN; st->done = 1; }
         st->nactive = bn == 0.0 ? 0 : ns;
+        st->fexp = 0;
+        st->sexp = 0;
         s_bn = bn;
     }
     __syncthreads();
@@ -343,6 +394,7 @@ __global__ void __launch_bounds__(kScalarThreads) k_init_state(SeedState* st, co
         sh.nblk[k] = 0;
         sh.iters[k] = 0;
         sh.resid[k] = 0.0;
+        sh.zexp[k] = 0;
     }
 }
 
@@ -367,7 +419,7 @@ struct SolverImpl {
     DevBuf<SeedState> state;
     DevBuf<double2> zeta, zeta_prev, shift, coef64;
     DevBuf<C> coefv;
-    DevBuf<int> active, conv, broken, nblk, iters;
+    DevBuf<int> active, conv, broken, nblk, iters, zexp;
     DevBuf<double> resid;
     DevBuf<double2> shifts_dev;
     ShiftArrays sh{};
@@ -375,17 +427,37 @@ struct SolverImpl {
 
     SolverImpl(const SolveProblem& p_, cudaStream_t s) : pr(p_), st(s) {}
 
+    const msb_op* op = nullptr;
+    size_t csz = sizeof(V);
+
     template <class View>
     void iteration(const View& view) {
         const int64_t n = pr.n;
-        k_mvm_dot<View, V><<<grid_vec, 256, 0, st>>>(view, p.p, v.p, n, pr.c0.x, pr.c0.y, state.p, part.p);
-        k_scalar_a<C><<<1, kScalarThreads, 0, st>>>(state.p, part.p, grid_vec, sh, pr.ns, B);
-        k_seed_update<V><<<grid_vec, 256, 0, st>>>(ring.p, v.p, n, nslot, state.p, part.p);
-        k_scalar_b<<<1, kScalarThreads, 0, st>>>(state.p, part.p, grid_vec, sh, pr.ns, nslot);
-        k_update_p<V><<<grid_vec, 256, 0, st>>>(ring.p, p.p, n, state.p);
+        const double nb = double(n) * csz;
+        {
+            ProfScope ps("seed_mvm", st, 2 * nb + op->matrix_bytes(csz), op->hx_flops() + 16.0 * n);
+            k_mvm_dot<View, V><<<grid_vec, 256, 0, st>>>(view, p.p, v.p, n, pr.c0.x, pr.c0.y, state.p, part.p);
+        }
+        {
+            ProfScope ps("shift_scalars", st, 0, 0);
+            k_scalar_a<C><<<1, kScalarThreads, 0, st>>>(state.p, part.p, grid_vec, sh, pr.ns, B);
+        }
+        {
+            ProfScope ps("seed_update", st, 3 * nb, 20.0 * n);
+            k_seed_update<V><<<grid_vec, 256, 0, st>>>(ring.p, v.p, n, nslot, state.p, part.p);
+        }
+        {
+            ProfScope ps("shift_scalars", st, 0, 0);
+            k_scalar_b<<<1, kScalarThreads, 0, st>>>(state.p, part.p, grid_vec, sh, pr.ns, nslot);
+        }
+        {
+            ProfScope ps("seed_p", st, 3 * nb, 8.0 * n);
+            k_update_p<V><<<grid_vec, 256, 0, st>>>(ring.p, p.p, n, state.p);
+        }
     }
 
     void flush() {
+        ProfScope ps("shift_update", st, 0, 0);
         switch (B) {
 #define MSB_FLUSH_CASE(BB)                                                                          \
     case BB:                                                                                        \
@@ -398,8 +470,21 @@ struct SolverImpl {
         }
     }
 
+    void one_block_direct(const void* viewp, bool hub) {
+        {
+            ProfScope ps("shift_scalars", st, 0, 0);
+            k_block_begin<<<1, kScalarThreads, 0, st>>>(state.p, sh, pr.ns);
+        }
+        for (int i = 0; i < B; ++i) {
+            if (hub) iteration(*(const HubView*)viewp);
+            else iteration(*(const CsrView*)viewp);
+        }
+        flush();
+    }
+
     template <class View>
-    void run(const View& view, SolveResult& out) {
+    void run(const msb_op* op_, const View& view, SolveResult& out) {
+        op = op_;
         const int64_t n = pr.n, ns = pr.ns;
         B = pr.block;
         nslot = B + 1;
@@ -414,18 +499,46 @@ struct SolverImpl {
         zeta.alloc(ns); zeta_prev.alloc(ns); shift.alloc(ns);
         coef64.alloc(size_t(ns) * B * 2);
         coefv.alloc(size_t(ns) * B * 2);
-        active.alloc(ns); conv.alloc(ns); broken.alloc(ns); nblk.alloc(ns); iters.alloc(ns);
+        active.alloc(ns); conv.alloc(ns); broken.alloc(ns); nblk.alloc(ns); iters.alloc(ns); zexp.alloc(ns);
         resid.alloc(ns);
         shifts_dev.alloc(ns);
         shifts_dev.upload(pr.shifts.data(), ns, st);
         sh = ShiftArrays{zeta.p, zeta_prev.p, shift.p, coef64.p, (void*)coefv.p,
-                         active.p, conv.p, broken.p, nblk.p, iters.p, resid.p};
+                         active.p, conv.p, broken.p, nblk.p, iters.p, resid.p, zexp.p};
 
-        k_init_vectors<V><<<grid_vec, 256, 0, st>>>((const V*)pr.b, ring.p, p.p, n, part.p);
-        k_init_state<<<1, kScalarThreads, 0, st>>>(state.p, part.p, grid_vec, sh, shifts_dev.p, int(ns),
-                                                    pr.tol, pr.maxit);
+        {
+            ProfScope ps("seed_init", st, 3.0 * n * csz, 12.0 * n);
+            k_init_vectors<V><<<grid_vec, 256, 0, st>>>((const V*)pr.b, ring.p, p.p, n, part.p);
+        }
+        {
+            ProfScope ps("shift_scalars", st, 0, 0);
+            k_init_state<<<1, kScalarThreads, 0, st>>>(state.p, part.p, grid_vec, sh, shifts_dev.p, int(ns),
+                                                        pr.tol, pr.maxit);
+        }
         launches += 2;
         MSB_LAUNCH_CHECK();
+        const int64_t per_block = 2 + 5 * int64_t(B);   // kernels per block of iterations
+        const int64_t max_blocks = (int64_t(pr.maxit) + B - 1) / B + 1;
+        int64_t blocks = 0;
+        if (prof_on()) {
+            // Profiled: direct launches, one sync per block to attribute the
+            // fused update's work (shifts and iterations it carried).
+            constexpr bool hub = std::is_same<View, HubView>::value;
+            SeedState hs;
+            for (;;) {
+                one_block_direct(&view, hub);
+                launches += per_block;
+                ++blocks;
+                MSB_CUDA(cudaMemcpyAsync(&hs, state.p, sizeof(SeedState), cudaMemcpyDeviceToHost, st));
+                MSB_CUDA(cudaStreamSynchronize(st));
+                const double no = double(pr.n_out) * csz;
+                prof_patch_last("shift_update", hs.flush_J * no + hs.flush_cnt * (hs.flush_first ? 2.0 : 4.0) * no,
+                                16.0 * hs.flush_cnt * hs.flush_J * double(pr.n_out));
+                if (hs.done || blocks > max_blocks + 2) break;
+            }
+            prof_collect();
+            out.flushes = blocks;
+        } else {
 
         // One block of B iterations + the fused per-shift update, captured once.
         cudaGraph_t graph = nullptr;
@@ -436,17 +549,14 @@ struct SolverImpl {
         flush();
         MSB_CUDA(cudaStreamEndCapture(st, &graph));
         MSB_CUDA(cudaGraphInstantiate(&exec, graph, 0));
-        const int64_t per_block = 2 + 5 * int64_t(B);   // kernels per replay
 
         HostBuf<SeedState> hstate(2);
         cudaEvent_t ev[2];
         MSB_CUDA(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
         MSB_CUDA(cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
-        int64_t blocks = 0;
         bool finished = false;
         // Two blocks in flight: launch block i, then look at the state copied
         // after block i-1.  Blocks launched after convergence return at once.
-        const int64_t max_blocks = (int64_t(pr.maxit) + B - 1) / B + 1;
         while (!finished) {
             MSB_CUDA(cudaGraphLaunch(exec, st));
             launches += per_block;
@@ -466,9 +576,11 @@ struct SolverImpl {
         cudaGraphExecDestroy(exec);
         cudaGraphDestroy(graph);
         out.flushes = blocks;
+        }
 
         SeedState fs;
-        MSB_CUDA(cudaMemcpy(&fs, state.p, sizeof(SeedState), cudaMemcpyDeviceToHost));
+        MSB_CUDA(cudaMemcpyAsync(&fs, state.p, sizeof(SeedState), cudaMemcpyDeviceToHost, st));
+        MSB_CUDA(cudaStreamSynchronize(st));
         if (fs.m == 0) {   // no iteration ran: solutions are zero
             k_zero<V><<<grid_for(ns * pr.n_out, 256, 8), 256, 0, st>>>((V*)pr.x, ns * pr.n_out);
             launches += 1;
@@ -480,10 +592,11 @@ struct SolverImpl {
         out.resid.resize(ns);
         out.conv.resize(ns);
         std::vector<int> brk(ns);
-        MSB_CUDA(cudaMemcpy(out.iters.data(), iters.p, ns * sizeof(int), cudaMemcpyDeviceToHost));
-        MSB_CUDA(cudaMemcpy(out.resid.data(), resid.p, ns * sizeof(double), cudaMemcpyDeviceToHost));
-        MSB_CUDA(cudaMemcpy(out.conv.data(), conv.p, ns * sizeof(int), cudaMemcpyDeviceToHost));
-        MSB_CUDA(cudaMemcpy(brk.data(), broken.p, ns * sizeof(int), cudaMemcpyDeviceToHost));
+        MSB_CUDA(cudaMemcpyAsync(out.iters.data(), iters.p, ns * sizeof(int), cudaMemcpyDeviceToHost, st));
+        MSB_CUDA(cudaMemcpyAsync(out.resid.data(), resid.p, ns * sizeof(double), cudaMemcpyDeviceToHost, st));
+        MSB_CUDA(cudaMemcpyAsync(out.conv.data(), conv.p, ns * sizeof(int), cudaMemcpyDeviceToHost, st));
+        MSB_CUDA(cudaMemcpyAsync(brk.data(), broken.p, ns * sizeof(int), cudaMemcpyDeviceToHost, st));
+        MSB_CUDA(cudaStreamSynchronize(st));
         out.status = msb_status(fs.status);
         int nconv = 0;
         for (int k = 0; k < ns; ++k) nconv += out.conv[k];
@@ -500,10 +613,10 @@ void multishift_solve(msb_op* op, const SolveProblem& pr, SolveResult& out, cuda
     MSB_REQUIRE(pr.ns >= 1 && pr.ns <= kMaxShifts, "n_shifts must be in 1..4096");
     if (pr.prec == MSB_FP64) {
         SolverImpl<double2> s(pr, st);
-        if (op->kind == 0) s.run(op->hub, out); else s.run(op->csr, out);
+        if (op->kind == 0) s.run(op, op->hub, out); else s.run(op, op->csr, out);
     } else {
         SolverImpl<float2> s(pr, st);
-        if (op->kind == 0) s.run(op->hub, out); else s.run(op->csr, out);
+        if (op->kind == 0) s.run(op, op->hub, out); else s.run(op, op->csr, out);
     }
 }
 

@@ -22,6 +22,7 @@ struct ShiftArrays {
     int* nblk;            // iterations of the current block to apply
     int* iters;           // iteration at freeze
     double* resid;        // ||r_m|| / (|zeta_m| ||b||) at freeze
+    int* zexp;            // E_k = log2(g_k / S_m): exponent of the stored zeta pair
 };
 
 struct SolveProblem {
@@ -73,7 +74,7 @@ struct CFResult {
 };
 void continued_fraction(msb_op* H, const void* phi, int n_vec, double E0, const double* w, int n_w,
                         double eta, double cf_tol, int cf_check, int cf_maxdepth, msb_precision prec,
-                        double* I_out, CFResult& out, cudaStream_t st);
+                        double* I_out, CFResult& out, cudaStream_t st, bool I_on_device = false);
 
 // Work runs on an internal non-blocking stream ordered after the caller's
 // stream; finish() orders the caller's stream after it and synchronises.

@@ -3,6 +3,7 @@
 
 #include "operator.cuh"
 #include "kernels.cuh"
+#include "profile.cuh"
 
 namespace msb {
 
@@ -40,6 +41,10 @@ static void build_hubbard(msb_op* op, const msb_model& m, int intermediate) {
     h.t = m.t; h.U = m.U; h.Uc = m.Uc;
     h.core = intermediate ? m.core_site : -1;
     op->dim = h.Dup * h.Ddn;
+    double nh = 0;
+    for (uint8_t c : cu) nh += double(c) * double(h.Ddn);
+    for (uint8_t c : cd) nh += double(c) * double(h.Dup);
+    op->offdiag = nh;
 }
 
 static void build_csr(msb_op* op, int64_t n, const int64_t* rowptr, const int32_t* col,
@@ -61,6 +66,7 @@ static void build_csr(msb_op* op, int64_t n, const int64_t* rowptr, const int32_
     op->val32.alloc(size_t(nnz)); op->val32.upload(v32.data(), size_t(nnz));
     MSB_CUDA(cudaDeviceSynchronize());
     op->csr = CsrView{n, op->rowptr.p, op->col.p, op->val64.p, op->val32.p};
+    op->offdiag = double(nnz);
 }
 
 // ---------------------------------------------------------------------------
@@ -80,9 +86,11 @@ __global__ void __launch_bounds__(256) k_apply(View op, const V* __restrict__ x,
 }
 
 template <class View>
-static void launch_apply(const View& v, int64_t n, double2 c0, const void* x, void* y, int nvec,
+static void launch_apply(const msb_op* op, const View& v, int64_t n, double2 c0, const void* x, void* y, int nvec,
                          msb_precision prec, cudaStream_t st) {
     dim3 grid(grid_for(n, 256, 8), nvec);
+    const size_t csz = prec == MSB_FP64 ? 16 : 8;
+    ProfScope ps("h_apply", st, nvec * (2.0 * n * csz + op->matrix_bytes(csz)), nvec * (op->hx_flops() + 8.0 * n));
     if (prec == MSB_FP64)
         k_apply<View, double2><<<grid, 256, 0, st>>>(v, (const double2*)x, (double2*)y, n, c0.x, c0.y);
     else
@@ -97,8 +105,9 @@ void op_apply(msb_op* op, double2 c0, const void* x, void* y, int nvec, msb_prec
     MSB_REQUIRE(x != nullptr && y != nullptr, "x / y is NULL");
     MSB_REQUIRE(nvec >= 1 && nvec <= 65535, "nvec must be in 1..65535");
     MSB_REQUIRE(prec == MSB_FP64 || prec == MSB_FP32_MIXED, "unknown precision");
-    if (op->kind == 0) launch_apply(op->hub, op->dim, c0, x, y, nvec, prec, st);
-    else launch_apply(op->csr, op->dim, c0, x, y, nvec, prec, st);
+    if (op->kind == 0) launch_apply(op, op->hub, op->dim, c0, x, y, nvec, prec, st);
+    else launch_apply(op, op->csr, op->dim, c0, x, y, nvec, prec, st);
+    prof_collect();
 }
 
 }  // namespace msb

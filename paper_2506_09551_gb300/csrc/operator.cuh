@@ -151,6 +151,16 @@ struct msb_op {
     msb::DevBuf<float> val32;
     msb::CsrView csr{};
     int device = 0;
+    double offdiag = 0;          // off-diagonal entries (hops, or CSR nonzeros)
+
+    // Floating-point operations of one application (A x)[all s] on complex
+    // vectors: two adds per hop plus the diagonal and hopping scale (Hubbard),
+    // or a complex-by-real multiply-add per nonzero (CSR).  Halve for real vectors.
+    double hx_flops() const { return kind == 0 ? 2.0 * offdiag + 6.0 * double(dim) : 4.0 * offdiag; }
+    // Bytes of the matrix itself read by one application (zero when matrix-free).
+    double matrix_bytes(size_t csz) const {
+        return kind == 0 ? 0.0 : offdiag * (4.0 + (csz == 16 ? 8.0 : 4.0)) + double(dim + 1) * 8.0;
+    }
 };
 
 namespace msb {

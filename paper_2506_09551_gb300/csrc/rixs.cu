@@ -19,6 +19,7 @@
 
 #include "kernels.cuh"
 #include "msbicg_impl.cuh"
+#include "profile.cuh"
 
 namespace msb {
 
@@ -90,7 +91,11 @@ static void launch_rowmap(const VS* x, VD* y, const std::vector<int32_t>& map, i
     DevBuf<int32_t> dmap(map.size());
     dmap.upload(map.data(), map.size(), st);
     const int64_t n = int64_t(map.size()) * Ddn;
-    k_rowmap<VS, VD><<<dim3(grid_for(n, 256, 8), nvec), 256, 0, st>>>(x, y, dmap.p, int64_t(map.size()), Ddn, ld_x, ld_y);
+    {
+        ProfScope ps("sector_map", st, double(nvec) * n * (sizeof(VS) + sizeof(VD)), 0);
+        k_rowmap<VS, VD><<<dim3(grid_for(n, 256, 8), nvec), 256, 0, st>>>(x, y, dmap.p, int64_t(map.size()), Ddn,
+                                                                           ld_x, ld_y);
+    }
     MSB_LAUNCH_CHECK();
     MSB_CUDA(cudaStreamSynchronize(st));   // dmap is freed on return
     ++launches;
@@ -117,8 +122,30 @@ static void apply_sector_map(const msb_model& m, int site, bool create, const vo
 // ---------------------------------------------------------------------------
 // The map
 // ---------------------------------------------------------------------------
+void rixs_map_core(msb_op* opH, msb_op* opHp, const msb_model& m, const msb_map_params& prm, const double* G_in,
+                   double E_G_in, const double* w_in, int n_in, const double* w, int n_w, double* I_out, bool I_dev,
+                   msb_solve_info& info, cudaStream_t st, int64_t launches_so_far);
+
 void rixs_map(const msb_model& m, const msb_map_params& prm, const double* G_in, double E_G_in, const double* w_in,
               int n_in, const double* w, int n_w, double* I_out, msb_solve_info& info, cudaStream_t st) {
+    validate_model(m);
+    MSB_REQUIRE(m.n_up + 1 <= m.L, "the intermediate sector needs n_up + 1 <= L");
+    std::unique_ptr<msb_op> opH, opHp;
+    {
+        msb_op* a = nullptr;
+        msb_status s1 = msb_op_create_hubbard(&m, 0, &a);
+        if (s1 != MSB_OK) fail(s1, msb_last_error());
+        opH.reset(a);
+        s1 = msb_op_create_hubbard(&m, 1, &a);
+        if (s1 != MSB_OK) fail(s1, msb_last_error());
+        opHp.reset(a);
+    }
+    rixs_map_core(opH.get(), opHp.get(), m, prm, G_in, E_G_in, w_in, n_in, w, n_w, I_out, false, info, st, 0);
+}
+
+void rixs_map_core(msb_op* opH_, msb_op* opHp_, const msb_model& m, const msb_map_params& prm, const double* G_in,
+                   double E_G_in, const double* w_in, int n_in, const double* w, int n_w, double* I_out, bool I_dev,
+                   msb_solve_info& info, cudaStream_t st, int64_t launches_so_far) {
     validate_model(m);
     MSB_REQUIRE(m.n_up + 1 <= m.L, "the intermediate sector needs n_up + 1 <= L");
     MSB_REQUIRE(n_in >= 1 && n_in <= kMaxShifts, "n_in must be in 1..4096");
@@ -130,18 +157,9 @@ void rixs_map(const msb_model& m, const msb_map_params& prm, const double* G_in,
     auto secs = [](std::chrono::steady_clock::time_point a) {
         return std::chrono::duration<double>(std::chrono::steady_clock::now() - a).count();
     };
-    int64_t launches = 0;
-    // operators
-    std::unique_ptr<msb_op> opH, opHp;
-    {
-        msb_op* a = nullptr;
-        msb_status s1 = msb_op_create_hubbard(&m, 0, &a);
-        if (s1 != MSB_OK) fail(s1, msb_last_error());
-        opH.reset(a);
-        s1 = msb_op_create_hubbard(&m, 1, &a);
-        if (s1 != MSB_OK) fail(s1, msb_last_error());
-        opHp.reset(a);
-    }
+    int64_t launches = launches_so_far;
+    struct { msb_op* get() const { return p; } msb_op* operator->() const { return p; } msb_op* p; } opH{opH_},
+        opHp{opHp_};
     const int64_t D = opH->dim, Dp = opHp->dim, Ddn = opH->hub.Ddn;
 
     // ground state
@@ -248,7 +266,7 @@ void rixs_map(const msb_model& m, const msb_map_params& prm, const double* G_in,
     t0 = std::chrono::steady_clock::now();
     CFResult cr;
     continued_fraction(opH.get(), Phi.p, n_in, E_G, w, n_w, prm.eta, prm.cf_tol, prm.cf_check, prm.cf_maxdepth,
-                       prm.precision, I_out, cr, st);
+                       prm.precision, I_out, cr, st, I_dev);
     launches += cr.launches;
     info.matvecs += cr.matvecs;
     int dmax = 0, dmin = 1 << 30;
@@ -281,6 +299,33 @@ extern "C" msb_status msb_apply_c_up(const msb_model* model, int site, const voi
     });
 }
 
+static bool same_model(const msb_model& a, const msb_model& b) {
+    return a.L == b.L && a.n_up == b.n_up && a.n_dn == b.n_dn && a.periodic == b.periodic && a.t == b.t &&
+           a.U == b.U && a.Uc == b.Uc && a.core_site == b.core_site;
+}
+
+extern "C" msb_status msb_rixs_map_ops(msb_op* H, msb_op* Hp, const msb_map_params* params, const double* G,
+                                       double E_G, const double* w_in, int n_in, const double* w, int n_w,
+                                       double* I_dev, msb_solve_info* info, void* stream) {
+    return msb::guard("msb_rixs_map_ops", [&] {
+        msb::require_device();
+        MSB_REQUIRE(H != nullptr && Hp != nullptr && params != nullptr, "NULL argument");
+        MSB_REQUIRE(H->kind == 0 && Hp->kind == 0 && !H->intermediate && Hp->intermediate,
+                    "H and Hp must be the Hubbard operators of one model (intermediate 0 and 1)");
+        MSB_REQUIRE(same_model(H->model, Hp->model), "H and Hp belong to different models");
+        msb::g_alloc_bytes = 0;
+        msb_solve_info local{};
+        msb::StreamScope scope((cudaStream_t)stream);
+        struct Fill {
+            msb_solve_info* dst; msb_solve_info* src;
+            ~Fill() { if (dst) { src->device_bytes = msb::g_alloc_bytes; *dst = *src; } }
+        } fill{info, &local};
+        msb::rixs_map_core(H, Hp, H->model, *params, G, E_G, w_in, n_in, w, n_w, I_dev, true, local, scope.s, 0);
+        scope.finish();
+        msb::prof_collect();
+    });
+}
+
 extern "C" msb_status msb_rixs_map(const msb_model* model, const msb_map_params* params, const double* G, double E_G,
                                    const double* w_in, int n_in, const double* w, int n_w, double* I_out,
                                    msb_solve_info* info, void* stream) {
@@ -296,5 +341,6 @@ extern "C" msb_status msb_rixs_map(const msb_model* model, const msb_map_params*
         } fill{info, &local};
         msb::rixs_map(*model, *params, G, E_G, w_in, n_in, w, n_w, I_out, local, scope.s);
         scope.finish();
+        msb::prof_collect();
     });
 }

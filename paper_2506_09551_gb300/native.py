@@ -45,6 +45,11 @@ class msb_solve_info(C.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class msb_kernel_stat(C.Structure):
+    _fields_ = [("name", C.c_char * 48), ("launches", C.c_int64), ("ms", C.c_double), ("alg_bytes", C.c_double),
+                ("alg_flops", C.c_double)]
+
+
 _P = C.c_void_p
 _I = C.c_int
 _D = C.c_double
@@ -74,7 +79,22 @@ SIGNATURES = {
     "msb_continued_fraction": (_I, [_P, _P, _I, _D, _PD, _I, _D, _D, _I, _I, _I, _PD, _PI, _P]),
     "msb_rixs_map": (_I, [C.POINTER(msb_model), C.POINTER(msb_map_params), _P, _D, _PD, _I, _PD, _I, _PD,
                           C.POINTER(msb_solve_info), _P]),
+    "msb_rixs_map_ops": (_I, [_P, _P, C.POINTER(msb_map_params), _P, _D, _PD, _I, _PD, _I, _P,
+                              C.POINTER(msb_solve_info), _P]),
+    "msb_profile_enable": (None, [_I]),
+    "msb_profile_reset": (None, []),
+    "msb_profile_read": (_I, [C.POINTER(msb_kernel_stat), _I]),
 }
+
+
+def profile_read() -> list:
+    """Per kernel class: dict(name, launches, ms, alg_bytes, alg_flops)."""
+    lib = load()
+    n = lib.msb_profile_read(None, 0)
+    arr = (msb_kernel_stat * max(n, 1))()
+    n = lib.msb_profile_read(arr, n)
+    return [dict(name=a.name.decode(), launches=a.launches, ms=a.ms, alg_bytes=a.alg_bytes, alg_flops=a.alg_flops)
+            for a in arr[:n]]
 
 
 class MsbError(RuntimeError):
