@@ -307,6 +307,7 @@ static bool same_model(const msb_model& a, const msb_model& b) {
 extern "C" msb_status msb_rixs_map_ops(msb_op* H, msb_op* Hp, const msb_map_params* params, const double* G,
                                        double E_G, const double* w_in, int n_in, const double* w, int n_w,
                                        double* I_dev, msb_solve_info* info, void* stream) {
+    if (info) *info = msb_solve_info{};
     return msb::guard("msb_rixs_map_ops", [&] {
         msb::require_device();
         MSB_REQUIRE(H != nullptr && Hp != nullptr && params != nullptr, "NULL argument");
@@ -329,6 +330,7 @@ extern "C" msb_status msb_rixs_map_ops(msb_op* H, msb_op* Hp, const msb_map_para
 extern "C" msb_status msb_rixs_map(const msb_model* model, const msb_map_params* params, const double* G, double E_G,
                                    const double* w_in, int n_in, const double* w, int n_w, double* I_out,
                                    msb_solve_info* info, void* stream) {
+    if (info) *info = msb_solve_info{};
     return msb::guard("msb_rixs_map", [&] {
         msb::require_device();
         MSB_REQUIRE(model != nullptr && params != nullptr, "NULL argument");
