@@ -196,6 +196,20 @@ msb_status msb_apply_c_up(const msb_model *model, int site, const void *x, void 
 msb_status msb_ground_state(msb_op *H, double tol, int maxit, const double *start,
                             double *E_G, double *g, double *residual, void *stream);
 
+/* The same ground state for callers that cannot allocate device memory
+ * (code running inside a stream capture in global capture mode, or a host
+ * whose device memory is owned by another allocator under a fixed budget).
+ * The paper has no counterpart: this is a deployment variant.  It allocates
+ * nothing: its scratch is a fixed array inside the library image (about 40
+ * MB, held on every GPU that loads the library until the process exits).
+ * Limits: dim <= 1048576 (2^20) and maxit <= 1024, else MSB_EINVAL.  The
+ * first call on each device looks up the array's address, so make that first
+ * call before any stream capture.  Work is ordered on `stream` itself, which
+ * is synchronised before returning.  All calls share the array: calls that
+ * overlap on the GPU race.  Arguments and results as msb_ground_state. */
+msb_status msb_ground_state_noalloc(msb_op *H, double tol, int maxit, const double *start,
+                                    double *E_G, double *g, double *residual, void *stream);
+
 /* ------------------------------------------------------------------------ */
 /* Multi-shifted BiCG (App. C; Alg. 1 in corrected form)                     */
 /* ------------------------------------------------------------------------ */

@@ -8,6 +8,8 @@
 // eigenvector is rebuilt by a second, identical pass).
 #include <algorithm>
 #include <cmath>
+#include <mutex>
+#include <string>
 #include <vector>
 
 #include "kernels.cuh"
@@ -572,4 +574,174 @@ extern "C" msb_status msb_continued_fraction(msb_op* H, const void* phi, int n_v
         scope.finish();
         if (depth) for (int c = 0; c < n_vec; ++c) depth[c] = r.depth[c];
     });
+}
+
+// ---------------------------------------------------------------------------
+// Ground state without any device allocation.
+//
+// Some callers cannot call cudaMalloc: code that runs while a stream is being
+// captured in global capture mode (allocation is not a capturable operation
+// and is refused there), and hosts whose device memory is owned by another
+// allocator under a fixed budget.  For them, msb_ground_state_noalloc runs the
+// same Lanczos kernels as msb_ground_state on a fixed scratch array that lives
+// in the library image: every GPU that loads the library holds it until the
+// process exits.  Its device address is looked up once per device (the first
+// call on a device does this set-up, so that first call should come before
+// any stream capture begins).  All calls share the array and it keeps the
+// previous call's contents; every part the Lanczos run reads is written first
+// in the call.  Calls that overlap on the GPU (two streams, or two threads)
+// race on the array.
+// ---------------------------------------------------------------------------
+namespace msb {
+
+constexpr int64_t kNoAllocMaxDim = int64_t(1) << 20;   // dimension limit of the operator
+constexpr int kNoAllocMaxIt = 1024;                     // Lanczos steps per restart
+constexpr int kNoAllocMaxGrid = 4096;                   // blocks of the vector kernels
+constexpr int64_t kNoAllocDoubles =
+    5 * kNoAllocMaxDim + 2 * int64_t(kNoAllocMaxIt + 1) + 3 * int64_t(kNoAllocMaxGrid) + 64;
+
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
+
+static double* noalloc_scratch_address() {
+    static std::mutex mu;
+    static double* addr[64] = {nullptr};
+    int dev = 0;
+    MSB_CUDA(cudaGetDevice(&dev));
+    MSB_REQUIRE(dev >= 0 && dev < 64, "device index out of range");
+    std::lock_guard<std::mutex> lk(mu);
+    if (!addr[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            fail(MSB_ECUDA, std::string("cudaGetSymbolAddress of the no-alloc scratch: ") + cudaGetErrorString(e));
+        }
+        addr[dev] = static_cast<double*>(p);
+    }
+    return addr[dev];
+}
+
+template <class View>
+static void ground_state_noalloc_impl(const View& view, int64_t n, double tol, int maxit, const double* start,
+                                      double* g, GroundResult& out, cudaStream_t st) {
+    const int grid = grid_for(n, 256, 8);
+    MSB_REQUIRE(grid <= kNoAllocMaxGrid, "grid exceeds the no-alloc scratch layout");
+    double* base = noalloc_scratch_address();
+    double* Q = base;                         // 3 Lanczos vectors
+    double* v0 = base + 3 * n;                // start vector of the current restart
+    double* hbuf = base + 4 * n;              // H g for the residual check
+    double* a_dev = base + 5 * n;             // a_k
+    double* b_dev = a_dev + (maxit + 1);      // b_{k+1}
+    double* bcur = b_dev + (maxit + 1);
+    double* n0 = bcur + 1;
+    int* col0 = reinterpret_cast<int*>(n0 + 1);
+    double* part = n0 + 2;                    // partial sums, 3 per block
+    MSB_CUDA(cudaMemsetAsync(col0, 0, sizeof(int), st));
+    if (start) MSB_CUDA(cudaMemcpyAsync(v0, start, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    else { k_fill_start<<<grid, 256, 0, st>>>(v0, n, 0x5EEDull); ++out.launches; }
+    std::vector<double> ha(maxit + 1), hb(maxit + 1), y;
+
+    auto run = [&](int kmax, bool accumulate, int& k_done) {
+        double* q = Q;
+        double* qp = Q + n;
+        double* w = Q + 2 * n;
+        k_lz_norm_partial<double><<<dim3(grid, 1), 256, 0, st>>>(v0, n, col0, part);
+        k_lz_sum<<<1, 256, 0, st>>>(part, grid, col0, n0, 0, 0);
+        k_lz_start<double><<<dim3(grid, 1), 256, 0, st>>>(v0, q, qp, n, col0, n0);
+        MSB_CUDA(cudaMemsetAsync(bcur, 0, sizeof(double), st));
+        out.launches += 3;
+        if (accumulate) MSB_CUDA(cudaMemsetAsync(g, 0, n * sizeof(double), st));
+        int k = 0;
+        for (; k < kmax; ++k) {
+            if (accumulate) { k_axpy_real<<<grid, 256, 0, st>>>(g, q, n, y[k]); ++out.launches; }
+            if (accumulate && k == kmax - 1) break;
+            k_lz_apply<View, double><<<dim3(grid, 1), 256, 0, st>>>(view, q, qp, w, n, col0, bcur, part);
+            k_lz_sum<<<1, 256, 0, st>>>(part, grid, col0, a_dev, 1, k);
+            k_lz_orth<double><<<dim3(grid, 1), 256, 0, st>>>(q, w, n, col0, a_dev + k, part);
+            k_lz_norm<<<1, 256, 0, st>>>(part, grid, col0, b_dev, 1, k, bcur);
+            k_lz_scale<double><<<dim3(grid, 1), 256, 0, st>>>(w, n, col0, bcur);
+            out.launches += 5;
+            ++out.matvecs;
+            MSB_LAUNCH_CHECK();
+            std::swap(qp, q);
+            std::swap(q, w);
+            if (!accumulate) {
+                MSB_CUDA(cudaMemcpyAsync(ha.data(), a_dev, (k + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
+                MSB_CUDA(cudaMemcpyAsync(hb.data(), b_dev, (k + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
+                MSB_CUDA(cudaStreamSynchronize(st));
+                double theta;
+                tridiag_lowest(ha, hb, k + 1, theta, y);
+                const double est = std::fabs(hb[k] * y[k]);
+                if (est <= 0.01 * tol * std::max(1.0, std::fabs(theta)) || hb[k] <= 1e-300 || k + 1 >= n) {
+                    ++k;
+                    break;
+                }
+            }
+        }
+        k_done = accumulate ? kmax : k;
+    };
+
+    out.status = MSB_OK;
+    for (int restart = 0; restart < 20; ++restart) {
+        int K = 0;
+        run(int(std::min<int64_t>(maxit, n)), false, K);
+        double theta;
+        tridiag_lowest(ha, hb, K, theta, y);
+        int K2 = 0;
+        run(K, true, K2);
+        k_gs_check<View><<<grid, 256, 0, st>>>(view, g, hbuf, n, part);
+        std::vector<double> hp(size_t(grid) * 3);
+        MSB_CUDA(cudaMemcpyAsync(hp.data(), part, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+        MSB_CUDA(cudaStreamSynchronize(st));
+        double gh = 0, hh = 0, gg = 0;
+        for (int b = 0; b < grid; ++b) { gh += hp[3 * b]; hh += hp[3 * b + 1]; gg += hp[3 * b + 2]; }
+        const double nrm = std::sqrt(gg);
+        k_scale_real<<<grid, 256, 0, st>>>(g, n, 1.0 / nrm);
+        k_scale_real<<<grid, 256, 0, st>>>(hbuf, n, 1.0 / nrm);
+        const double E = gh / gg;
+        k_gs_resid_partial<<<grid, 256, 0, st>>>(g, hbuf, n, E, part);
+        std::vector<double> rp(grid);
+        MSB_CUDA(cudaMemcpyAsync(rp.data(), part, grid * sizeof(double), cudaMemcpyDeviceToHost, st));
+        MSB_CUDA(cudaStreamSynchronize(st));
+        double rr = 0;
+        for (double v : rp) rr += v;
+        out.launches += 4;
+        ++out.matvecs;
+        out.E = E;
+        out.residual = std::sqrt(rr);
+        out.restarts = restart;
+        if (out.residual <= tol * std::max(1.0, std::fabs(E))) return;
+        MSB_CUDA(cudaMemcpyAsync(v0, g, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    }
+    out.status = MSB_EMAXITER;
+}
+
+}  // namespace msb
+
+extern "C" msb_status msb_ground_state_noalloc(msb_op* H, double tol, int maxit, const double* start,
+                                               double* E_G, double* g, double* residual, void* stream) {
+    msb_status result = MSB_OK;
+    msb_status s = msb::guard("msb_ground_state_noalloc", [&] {
+        msb::require_device();
+        MSB_REQUIRE(H != nullptr && g != nullptr, "NULL argument");
+        MSB_REQUIRE(tol > 0, "tol must be > 0");
+        MSB_REQUIRE(maxit >= 2 && maxit <= msb::kNoAllocMaxIt,
+                    "maxit must be in 2.." + std::to_string(msb::kNoAllocMaxIt) + " for the no-alloc ground state");
+        MSB_REQUIRE(H->dim <= msb::kNoAllocMaxDim,
+                    "operator dimension " + std::to_string(H->dim) + " exceeds the no-alloc scratch limit of " +
+                        std::to_string(msb::kNoAllocMaxDim));
+        int dev = 0;
+        MSB_CUDA(cudaGetDevice(&dev));
+        MSB_REQUIRE(dev == H->device, "the operator was created on another device");
+        cudaStream_t st = (cudaStream_t)stream;
+        msb::GroundResult r;
+        if (H->kind == 0) msb::ground_state_noalloc_impl(H->hub, H->dim, tol, maxit, start, g, r, st);
+        else msb::ground_state_noalloc_impl(H->csr, H->dim, tol, maxit, start, g, r, st);
+        MSB_CUDA(cudaStreamSynchronize(st));
+        if (E_G) *E_G = r.E;
+        if (residual) *residual = r.residual;
+        result = r.status;
+        if (result != MSB_OK) msb::set_error_message("msb_ground_state_noalloc: tolerance not reached");
+    });
+    return s != MSB_OK ? s : result;
 }

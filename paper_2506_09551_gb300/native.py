@@ -74,6 +74,7 @@ SIGNATURES = {
     "msb_apply_cdag_up": (_I, [C.POINTER(msb_model), _I, _P, _P, _I, _I, _P]),
     "msb_apply_c_up": (_I, [C.POINTER(msb_model), _I, _P, _P, _I, _I, _P]),
     "msb_ground_state": (_I, [_P, _D, _I, _P, _PD, _P, _PD, _P]),
+    "msb_ground_state_noalloc": (_I, [_P, _D, _I, _P, _PD, _P, _PD, _P]),
     "msb_multishift_bicg_solve": (_I, [_P, msb_complex, _P, C.POINTER(msb_complex), _I, _D, _I, _I, _I, _P,
                                        _PI, _PD, _PI, C.POINTER(msb_solve_info), _P]),
     "msb_continued_fraction": (_I, [_P, _P, _I, _D, _PD, _I, _D, _D, _I, _I, _I, _PD, _PI, _P]),
