@@ -69,6 +69,8 @@ class ClockSampler:
         self.path = None
 
     def __enter__(self):
+        if self.gpu is None:
+            return self
         fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
         os.close(fd)
         try:
@@ -88,6 +90,8 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
+        if self.path is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["not sampled (--no-clocks)"]}
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         try:
@@ -219,6 +223,8 @@ def gpu_arm(args, rank, world):
     H = api.Operator.hubbard(m, False)
     Hp = api.Operator.hubbard(m, True)
     w_in, w = wl.w_in, wl.w
+    if args.n_in:
+        w_in = np.linspace(wl.w_in_range[0], wl.w_in_range[1], args.n_in)
     out = torch.empty((len(w_in), len(w)), dtype=torch.float64, device="cuda")
 
     def barrier():
@@ -242,7 +248,7 @@ def gpu_arm(args, rank, world):
         gpu_id = "GPU-" + str(u) if not str(u).startswith("GPU-") else str(u)
     except Exception:
         pass
-    with ClockSampler(gpu_id) as clk:
+    with ClockSampler(None if args.no_clocks else gpu_id) as clk:
         torch.cuda.synchronize()
         barrier()
         e0.record(stream)
@@ -306,7 +312,7 @@ def gpu_arm(args, rank, world):
         "dtype": "c128" if prec == 0 else "c64 vectors, f64 scalars",
         "data": "synthetic: 1D Hubbard ring, random-start Lanczos ground state",
         "config": {"workload": args.workload, "L": wl.L, "n_up": wl.n_up, "n_dn": wl.n_dn,
-                   "dim_ground": int(H.dim), "dim_intermediate": int(Hp.dim), "n_w_in": wl.n_in, "n_w": wl.n_w,
+                   "dim_ground": int(H.dim), "dim_intermediate": int(Hp.dim), "n_w_in": len(w_in), "n_w": len(w),
                    "Gamma": wl.Gamma, "eta": wl.eta, "solve_tol": stol, "cf_tol": ctol,
                    "precision": "FP64" if prec == 0 else "FP32-mixed",
                    "parallelism": f"{world} independent maps (core site = rank)",
@@ -359,6 +365,8 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end map (profiling runs)")
+    ap.add_argument("--no-clocks", action="store_true", help="do not sample nvidia-smi (profiling runs)")
+    ap.add_argument("--n-in", type=int, default=0, help="incident energies (0: the workload's; profiling runs)")
     ap.add_argument("--cpu-baseline-worker", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()
 

@@ -24,9 +24,34 @@ __device__ __forceinline__ void bil_acc(double2 u, double2 v, double& re, double
     re = fma(u.x, v.x, fma(-u.y, v.y, re));
     im = fma(u.x, v.y, fma(u.y, v.x, im));
 }
-// FP32 operands: the product of two floats is exact in double.
-__device__ __forceinline__ void bil_acc(float2 u, float2 v, double& re, double& im) {
-    bil_acc(make_double2(u.x, u.y), make_double2(v.x, v.y), re, im);
+// Compensated accumulation of products in the FP32 pipe.  GB300 issues FP64 at
+// 1/64 of the FP32 rate, so per-element FP64 work would bound the FP32 path.
+// hi + lo carries the running sum of x*y to about 2^-48 relative: the product
+// is split exactly with an FMA (TwoProduct) and added with Knuth's TwoSum; the
+// _rn intrinsics keep the compiler from contracting the error terms away.
+// The pair is converted to FP64 once per thread (df_value).
+__device__ __forceinline__ void df_add_prod(float& hi, float& lo, float x, float y) {
+    const float p = __fmul_rn(x, y);
+    const float pe = __fmaf_rn(x, y, -p);
+    const float s = __fadd_rn(hi, p);
+    const float bb = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(e, pe));
+}
+__device__ __forceinline__ double df_value(float hi, float lo) { return double(hi) + double(lo); }
+
+// Compensated accumulators of a bilinear product (re, im) and a squared norm.
+struct DF4 { float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f, nh = 0.f, nl = 0.f; };
+__device__ __forceinline__ void bil_acc_df(float2 u, float2 v, DF4& a) {
+    df_add_prod(a.rh, a.rl, u.x, v.x);
+    df_add_prod(a.rh, a.rl, -u.y, v.y);
+    df_add_prod(a.ih, a.il, u.x, v.y);
+    df_add_prod(a.ih, a.il, u.y, v.x);
+}
+__device__ __forceinline__ void norm_acc_df(float2 v, DF4& a) {
+    df_add_prod(a.nh, a.nl, v.x, v.x);
+    df_add_prod(a.nh, a.nl, v.y, v.y);
 }
 // Hermitian product term conj(u) * v accumulated into (re, im).
 __device__ __forceinline__ void her_acc(double2 u, double2 v, double& re, double& im) {

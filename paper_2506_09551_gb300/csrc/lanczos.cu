@@ -429,70 +429,362 @@ __global__ void k_cf_eval(const double* __restrict__ a, const double* __restrict
     }
 }
 
-template <class View, typename V>
+// ---------------------------------------------------------------------------
+// Continued-fraction Lanczos with unnormalised vectors.  Column c stores V_k
+// with q_k = sig_k V_k, so no pass rescales a vector:
+//   pass A:  W = sig_k (H V_k) - (b_k sig_{k-1}) V_{k-1};   a_k = sig_k Re<V_k|W>
+//   pass B:  W -= (a_k sig_k) V_k;                           b_{k+1} = ||W||
+//   then V_{k+1} = W, sig_{k+1} = 1 / b_{k+1} (0 once the Krylov space is exhausted).
+// Columns are stored with a stride `ld` (n rounded up to 2) for 16-byte loads;
+// the padding stays zero.  In the FP32 path every product is accumulated with
+// the compensated FP32 scheme of df_add_prod (no per-element FP64 work).
+// ---------------------------------------------------------------------------
+struct CFCoef {
+    double* sig;      // sig_k per column
+    double* cB;       // b_k sig_{k-1} per column (0 at k = 0)
+    double* cC;       // a_k sig_k per column
+};
+
+constexpr int kMaxHops = 16;
+
+// Pass A for the Hubbard operator, one CTA per (row u, active column): row u
+// of V_k is staged in shared memory (own values and the down-spin gathers);
+// the up-spin hops read rows u' of V_k coalesced along d.  All CTAs of one
+// column are adjacent in launch order, so the column being gathered from stays
+// in L2; V_{k-1} and W are streamed with evict-first hints so they do not push
+// it out.  Offsets inside a column are 32-bit (fewer than 2^31 elements for
+// L <= 16).
+template <typename C>
+__global__ void __launch_bounds__(256, 6) k_cf_apply_hub(HubView h, const C* __restrict__ Vk,
+                                                         const C* __restrict__ Vkm1, C* __restrict__ W, int64_t ld,
+                                                         const int* __restrict__ cols, CFCoef cf, double* part,
+                                                         int L) {
+    using S = scalar_t<C>;
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    C* row = reinterpret_cast<C*>(sm_raw);                          // Ddn values of row u
+    S* lut = reinterpret_cast<S*>(row + h.Ddn);                     // 3 (L + 1) diagonal values * sig
+    __shared__ int s_uoff[kMaxHops];
+    __shared__ S s_usg[kMaxHops];
+    __shared__ double red[32];
+    const int c = cols[blockIdx.y];
+    const int u = blockIdx.x;
+    const int Ddn = int(h.Ddn);
+    const C* __restrict__ Vc = Vk + int64_t(c) * ld;
+    const C* __restrict__ Pc = Vkm1 + int64_t(c) * ld;
+    C* __restrict__ Wc = W + int64_t(c) * ld;
+    const int rbase = u * Ddn;
+    const double sig = cf.sig[c], cB = cf.cB[c];
+    const bool has_prev = cB != 0.0;
+    const uint32_t su = __ldg(h.sup + u);
+    const int nu = __ldg(h.nup + u);
+    for (int d = threadIdx.x; d < Ddn; d += blockDim.x) row[d] = Vc[rbase + d];
+    for (int i = threadIdx.x; i < 3 * (L + 1); i += blockDim.x) {
+        const int p = i % (L + 1), nb = i / (L + 1);
+        lut[i] = S(sig * (h.U * double(p) - h.Uc * double(nb)));
+    }
+    if (threadIdx.x < nu) {
+        const int32_t ent = __ldg(h.hup + int64_t(threadIdx.x) * h.Dup + u);
+        s_uoff[threadIdx.x] = (ent >> 1) * Ddn;
+        s_usg[threadIdx.x] = (ent & 1) ? S(-1) : S(1);
+    }
+    __syncthreads();
+    const int core = h.core;
+    const int ubits = core >= 0 ? int((su >> core) & 1u) : 0;
+    const S mt = S(-h.t * sig);
+    const S mcB = S(-cB);
+    double dot = 0.0;
+    float dhi = 0.f, dlo = 0.f;
+    for (int d = threadIdx.x; d < Ddn; d += blockDim.x) {
+        S ax = 0, ay = 0;
+        for (int e = 0; e < nu; ++e) {
+            const C v = Vc[s_uoff[e] + d];
+            const S sg = s_usg[e];
+            ax = fma(sg, v.x, ax);
+            ay = fma(sg, v.y, ay);
+        }
+        const int nd = __ldg(h.ndn + d);
+        for (int e = 0; e < nd; ++e) {
+            const int32_t hh = __ldg(h.hdn + e * Ddn + d);
+            const C v = row[hh >> 1];
+            const S sg = (hh & 1) ? S(-1) : S(1);
+            ax = fma(sg, v.x, ax);
+            ay = fma(sg, v.y, ay);
+        }
+        const uint32_t sd = __ldg(h.sdn + d);
+        const int nb = core >= 0 ? ubits + int((sd >> core) & 1u) : 0;
+        const S dg = lut[__popc(su & sd) + nb * (L + 1)];
+        const C x = row[d];
+        C wv;
+        wv.x = fma(mt, ax, dg * x.x);
+        wv.y = fma(mt, ay, dg * x.y);
+        if (has_prev) {
+            const C y = __ldcs(Pc + rbase + d);
+            wv.x = fma(mcB, y.x, wv.x);
+            wv.y = fma(mcB, y.y, wv.y);
+        }
+        __stcs(Wc + rbase + d, wv);
+        if constexpr (std::is_same<S, float>::value) {
+            df_add_prod(dhi, dlo, x.x, wv.x);
+            df_add_prod(dhi, dlo, x.y, wv.y);
+        } else {
+            dot = fma(x.x, wv.x, fma(x.y, wv.y, dot));
+        }
+    }
+    if constexpr (std::is_same<S, float>::value) dot = df_value(dhi, dlo);
+    double acc[1] = {dot};
+    block_sum<1>(acc, red);
+    if (threadIdx.x == 0) part[int64_t(blockIdx.y) * gridDim.x + blockIdx.x] = acc[0];
+}
+
+// Pass A for any operator view (CSR): flat grid over elements.
+template <class View, typename C>
+__global__ void __launch_bounds__(256) k_cf_apply_gen(View op, const C* __restrict__ Vk, const C* __restrict__ Vkm1,
+                                                      C* __restrict__ W, int64_t n, int64_t ld,
+                                                      const int* __restrict__ cols, CFCoef cf, double* part) {
+    using S = scalar_t<C>;
+    __shared__ double sm[32];
+    const int c = cols[blockIdx.y];
+    const int64_t off = int64_t(c) * ld;
+    const S sig = S(cf.sig[c]), mcB = S(-cf.cB[c]);
+    const bool has_prev = cf.cB[c] != 0.0;
+    double dot = 0.0;
+    float dhi = 0.f, dlo = 0.f;
+    for (int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < n; s += int64_t(gridDim.x) * blockDim.x) {
+        const C x = Vk[off + s];
+        const C hx = op.hx(s, Vk + off, x);
+        C wv = mk(sig * hx.x, sig * hx.y);
+        if (has_prev) {
+            const C y = Vkm1[off + s];
+            wv.x = fma(mcB, y.x, wv.x);
+            wv.y = fma(mcB, y.y, wv.y);
+        }
+        W[off + s] = wv;
+        if constexpr (std::is_same<S, float>::value) {
+            df_add_prod(dhi, dlo, x.x, wv.x);
+            df_add_prod(dhi, dlo, x.y, wv.y);
+        } else {
+            dot = fma(x.x, wv.x, fma(x.y, wv.y, dot));
+        }
+    }
+    if constexpr (std::is_same<S, float>::value) dot = df_value(dhi, dlo);
+    double acc[1] = {dot};
+    store_partials<1>(acc, sm, part);
+}
+
+// a_k = sig_k * sum;  cC = a_k sig_k.
+__global__ void k_cf_reduce_a(const double* part, int nblk, const int* cols, double* astore, int64_t stride_k, int k,
+                              CFCoef cf) {
+    __shared__ double sm[32];
+    const int c = cols[blockIdx.x];
+    double v[1];
+    reduce_partials<1>(part + int64_t(blockIdx.x) * nblk, nblk, v, sm);
+    if (threadIdx.x == 0) {
+        const double a = cf.sig[c] * v[0];
+        astore[int64_t(k) * stride_k + c] = a;
+        cf.cC[c] = a * cf.sig[c];
+    }
+}
+
+// W -= cC V_k; partial ||W||^2.  16-byte loads: one complex double or two
+// complex floats (ld is even and the padding is zero).
+__device__ __forceinline__ void orth_step(double2 v, double2& x, double m, double& acc, float&, float&) {
+    x.x = fma(m, v.x, x.x);
+    x.y = fma(m, v.y, x.y);
+    acc = fma(x.x, x.x, acc);
+    acc = fma(x.y, x.y, acc);
+}
+__device__ __forceinline__ void orth_step(float4 v, float4& x, float m, double&, float& hi, float& lo) {
+    x.x = fmaf(m, v.x, x.x);
+    x.y = fmaf(m, v.y, x.y);
+    x.z = fmaf(m, v.z, x.z);
+    x.w = fmaf(m, v.w, x.w);
+    df_add_prod(hi, lo, x.x, x.x);
+    df_add_prod(hi, lo, x.y, x.y);
+    df_add_prod(hi, lo, x.z, x.z);
+    df_add_prod(hi, lo, x.w, x.w);
+}
+
+template <typename C>
+__global__ void __launch_bounds__(256) k_cf_orth(const C* __restrict__ Vk, C* __restrict__ W, int64_t ld,
+                                                 const int* __restrict__ cols, CFCoef cf, double* part) {
+    using S = scalar_t<C>;
+    using V16 = typename std::conditional<std::is_same<S, float>::value, float4, double2>::type;
+    constexpr int per = sizeof(V16) / sizeof(C);     // complex elements per 16-byte load
+    __shared__ double sm[32];
+    const int c = cols[blockIdx.y];
+    const V16* __restrict__ v4 = reinterpret_cast<const V16*>(Vk + int64_t(c) * ld);
+    V16* __restrict__ w4 = reinterpret_cast<V16*>(W + int64_t(c) * ld);
+    const int64_t nv = ld / per;
+    const S mc = S(-cf.cC[c]);
+    double acc = 0.0;
+    float hi = 0.f, lo = 0.f;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    for (; i + stride < nv; i += 2 * stride) {      // two independent loads in flight per stream
+        V16 x0 = w4[i], x1 = w4[i + stride];
+        const V16 a0 = v4[i], a1 = v4[i + stride];
+        orth_step(a0, x0, mc, acc, hi, lo);
+        orth_step(a1, x1, mc, acc, hi, lo);
+        w4[i] = x0;
+        w4[i + stride] = x1;
+    }
+    if (i < nv) {
+        V16 x0 = w4[i];
+        orth_step(v4[i], x0, mc, acc, hi, lo);
+        w4[i] = x0;
+    }
+    if constexpr (std::is_same<S, float>::value) acc = df_value(hi, lo);
+    double a1[1] = {acc};
+    store_partials<1>(a1, sm, part);
+}
+
+// b_{k+1} = ||W||; next step: cB = b_{k+1} sig_k, sig = 1 / b_{k+1}.
+__global__ void k_cf_reduce_b(const double* part, int nblk, const int* cols, double* bstore, int64_t stride_k, int k,
+                              CFCoef cf) {
+    __shared__ double sm[32];
+    const int c = cols[blockIdx.x];
+    double v[1];
+    reduce_partials<1>(part + int64_t(blockIdx.x) * nblk, nblk, v, sm);
+    if (threadIdx.x == 0) {
+        const double b = sqrt(v[0]);
+        bstore[int64_t(k) * stride_k + c] = b;
+        cf.cB[c] = b * cf.sig[c];
+        cf.sig[c] = b > 0.0 ? 1.0 / b : 0.0;
+    }
+}
+
+// V_0 = phi (copied: the input is not modified; padding zeroed); the other two
+// vector blocks get a zero padding; partial ||phi||^2.
+template <typename C>
+__global__ void __launch_bounds__(256) k_cf_start(const C* __restrict__ phi, C* __restrict__ V0, C* __restrict__ V1,
+                                                  C* __restrict__ V2, int64_t n, int64_t ld, double* part) {
+    using S = scalar_t<C>;
+    __shared__ double sm[32];
+    const int c = blockIdx.y;
+    double acc = 0.0;
+    float hi = 0.f, lo = 0.f;
+    for (int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < ld; s += int64_t(gridDim.x) * blockDim.x) {
+        C x = mk(S(0), S(0));
+        if (s < n) x = phi[int64_t(c) * n + s];
+        V0[int64_t(c) * ld + s] = x;
+        if (s >= n) {
+            V1[int64_t(c) * ld + s] = x;
+            V2[int64_t(c) * ld + s] = x;
+        }
+        if constexpr (std::is_same<S, float>::value) {
+            df_add_prod(hi, lo, x.x, x.x);
+            df_add_prod(hi, lo, x.y, x.y);
+        } else {
+            acc = fma(x.x, x.x, fma(x.y, x.y, acc));
+        }
+    }
+    if constexpr (std::is_same<S, float>::value) acc = df_value(hi, lo);
+    double a1[1] = {acc};
+    store_partials<1>(a1, sm, part);
+}
+
+// n0 = ||phi||^2, sig_0 = 1/sqrt(n0), cB = 0 (one CTA per column).
+__global__ void k_cf_setup(const double* part, int nblk, double* n0, CFCoef cf) {
+    __shared__ double sm[32];
+    const int c = blockIdx.x;
+    double v[1];
+    reduce_partials<1>(part + int64_t(c) * nblk, nblk, v, sm);
+    if (threadIdx.x == 0) {
+        n0[c] = v[0];
+        cf.sig[c] = v[0] > 0.0 ? 1.0 / sqrt(v[0]) : 0.0;
+        cf.cB[c] = 0.0;
+        cf.cC[c] = 0.0;
+    }
+}
+
+template <class View, typename C>
 static void cf_impl(const msb_op* op, const View& view, int64_t n, const void* phi_v, int nv, double E0, const double* w,
                     int n_w, double eta, double cf_tol, int check, int maxdepth, double* I_out, CFResult& out,
                     cudaStream_t st, bool I_dev) {
-    const double vb = double(sizeof(V)) * double(n);        // one complex vector
-    const V* phi = (const V*)phi_v;
-    const int grid = grid_for(n, 256, 4);
-    DevBuf<V> Q(3 * size_t(nv) * n);
-    DevBuf<double> part(size_t(grid) * nv), a(size_t(maxdepth) * nv), b(size_t(maxdepth) * nv), n0(nv),
-        bcur(nv), I(size_t(nv) * n_w), diff(2 * size_t(nv)), wdev(n_w);
+    constexpr bool hub = std::is_same<View, HubView>::value;
+    const int64_t ld = (n + 1) / 2 * 2;
+    const double vb = double(sizeof(C)) * double(n);        // one complex vector
+    const C* phi = (const C*)phi_v;
+    const int per = int(16 / sizeof(C));
+    const int grid = grid_for(ld / per, 256, 4);
+    int64_t hub_smem = 0;
+    int L = 0;
+    bool rows = false;
+    int nblkA = grid;
+    if constexpr (hub) {
+        L = op->model.L;
+        hub_smem = view.Ddn * int64_t(sizeof(C)) + 3 * (L + 1) * 8;
+        rows = hub_smem <= 160 * 1024 && view.Wup <= kMaxHops && view.Dup * view.Ddn < (int64_t(1) << 31);
+        if (rows) {
+            nblkA = int(view.Dup);
+            MSB_CUDA(cudaFuncSetAttribute(k_cf_apply_hub<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          int(hub_smem)));
+        }
+    }
+    DevBuf<C> Q(3 * size_t(nv) * ld);
+    DevBuf<double> part(size_t(std::max(grid, nblkA)) * nv), a(size_t(maxdepth) * nv), b(size_t(maxdepth) * nv),
+        n0(nv), sig(nv), cB(nv), cC(nv), I(size_t(nv) * n_w), diff(2 * size_t(nv)), wdev(n_w);
     DevBuf<int> cols(nv), depth(nv);
+    CFCoef cf{sig.p, cB.p, cC.p};
     wdev.upload(w, n_w, st);
-    std::vector<int> hcols(nv), hdepth(nv, 0), active(nv, 1);
-    for (int c = 0; c < nv; ++c) hcols[c] = c;
-    cols.upload(hcols.data(), nv, st);
+    std::vector<int> hcols(nv), hdepth(nv, 0);
     MSB_CUDA(cudaMemsetAsync(I.p, 0, I.bytes(), st));
-    MSB_CUDA(cudaMemsetAsync(bcur.p, 0, bcur.bytes(), st));
-    V* q = Q.p;
-    V* qp = Q.p + size_t(nv) * n;
-    V* wv = Q.p + 2 * size_t(nv) * n;
-    // start vectors
-    k_lz_norm_partial<V><<<dim3(grid, nv), 256, 0, st>>>(phi, n, cols.p, part.p);
-    k_lz_sum<<<nv, 256, 0, st>>>(part.p, grid, cols.p, n0.p, 0, 0);
-    k_lz_start<V><<<dim3(grid, nv), 256, 0, st>>>(phi, q, qp, n, cols.p, n0.p);
-    out.launches += 3;
+    C* vk = Q.p;
+    C* vkm1 = Q.p + size_t(nv) * ld;
+    C* wv = Q.p + 2 * size_t(nv) * ld;
+    {
+        ProfScope ps("cf_start", st, nv * 2 * vb, nv * 4.0 * n);
+        k_cf_start<C><<<dim3(grid, nv), 256, 0, st>>>(phi, vk, vkm1, wv, n, ld, part.p);
+    }
+    { ProfScope ps("cf_reduce", st, 0, 0); k_cf_setup<<<nv, 256, 0, st>>>(part.p, grid, n0.p, cf); }
+    out.launches += 2;
     MSB_LAUNCH_CHECK();
-    std::vector<double> hn0(nv), hb(nv), hdiff(2 * size_t(nv));
+    std::vector<double> hn0(nv), hdiff(2 * size_t(nv));
     MSB_CUDA(cudaMemcpyAsync(hn0.data(), n0.p, nv * sizeof(double), cudaMemcpyDeviceToHost, st));
     MSB_CUDA(cudaStreamSynchronize(st));
     int nact = 0;
-    for (int c = 0; c < nv; ++c) {
+    for (int c = 0; c < nv; ++c)
         if (hn0[c] > 0.0) hcols[nact++] = c;
-        else active[c] = 0;
-    }
-    cols.upload(hcols.data(), nact, st);
-    std::vector<double> scale(nv, 0.0);
+    cols.upload(hcols.data(), std::max(nact, 1), st);
     int k = 0;
     while (nact > 0 && k < maxdepth) {
-        const dim3 g2(grid, nact);
         {
-            ProfScope ps("cf_apply", st, nact * (3 * vb + op->matrix_bytes(sizeof(V))),
+            ProfScope ps("cf_apply", st, nact * (3 * vb + op->matrix_bytes(sizeof(C))),
                          nact * (op->hx_flops() + 8.0 * n));
-            k_lz_apply<View, V><<<g2, 256, 0, st>>>(view, q, qp, wv, n, cols.p, bcur.p, part.p);
+            bool done_hub = false;
+            if constexpr (hub) {
+                if (rows) {
+                    k_cf_apply_hub<C><<<dim3(unsigned(nblkA), nact), 256, hub_smem, st>>>(view, vk, vkm1, wv, ld,
+                                                                                          cols.p, cf, part.p, L);
+                    done_hub = true;
+                }
+            }
+            if (!done_hub)
+                k_cf_apply_gen<View, C><<<dim3(grid, nact), 256, 0, st>>>(view, vk, vkm1, wv, n, ld, cols.p, cf,
+                                                                          part.p);
         }
-        { ProfScope ps("cf_reduce", st, 0, 0); k_lz_sum<<<nact, 256, 0, st>>>(part.p, grid, cols.p, a.p, nv, k); }
+        {
+            ProfScope ps("cf_reduce", st, 0, 0);
+            k_cf_reduce_a<<<nact, 256, 0, st>>>(part.p, rows ? nblkA : grid, cols.p, a.p, nv, k, cf);
+        }
         {
             ProfScope ps("cf_orth", st, nact * 3 * vb, nact * 8.0 * n);
-            k_lz_orth<V><<<g2, 256, 0, st>>>(q, wv, n, cols.p, a.p + int64_t(k) * nv, part.p);
+            k_cf_orth<C><<<dim3(grid, nact), 256, 0, st>>>(vk, wv, ld, cols.p, cf, part.p);
         }
-        { ProfScope ps("cf_reduce", st, 0, 0); k_lz_norm<<<nact, 256, 0, st>>>(part.p, grid, cols.p, b.p, nv, k, bcur.p); }
         {
-            ProfScope ps("cf_scale", st, nact * 2 * vb, nact * 2.0 * n);
-            k_lz_scale<V><<<g2, 256, 0, st>>>(wv, n, cols.p, bcur.p);
+            ProfScope ps("cf_reduce", st, 0, 0);
+            k_cf_reduce_b<<<nact, 256, 0, st>>>(part.p, grid, cols.p, b.p, nv, k, cf);
         }
-        out.launches += 5;
+        out.launches += 4;
         out.matvecs += nact;
         MSB_LAUNCH_CHECK();
-        std::swap(qp, q);
-        std::swap(q, wv);
+        // (V_{k-1}, V_k, W) <- (V_k, W, V_{k-1})
+        C* t = vkm1;
+        vkm1 = vk;
+        vk = wv;
+        wv = t;
         ++k;
         if (k % check == 0 || k == maxdepth) {
-            // exhausted Krylov spaces and converged rows
-            MSB_CUDA(cudaMemcpyAsync(hb.data(), b.p + int64_t(k - 1) * nv, nv * sizeof(double),
-                                     cudaMemcpyDeviceToHost, st));
             for (int i = 0; i < nact; ++i) hdepth[hcols[i]] = k;
             depth.upload(hdepth.data(), nv, st);
             {
@@ -508,16 +800,12 @@ static void cf_impl(const msb_op* op, const View& view, int64_t n, const void* p
                 const int c = hcols[i];
                 bool fin = k >= maxdepth;
                 if (k > check && hdiff[2 * c] <= cf_tol * hdiff[2 * c + 1]) fin = true;
-                if (fin) active[c] = 0;
-                else hcols[keep++] = c;
+                if (!fin) hcols[keep++] = c;
             }
             nact = keep;
             cols.upload(hcols.data(), std::max(nact, 1), st);
         }
     }
-    // Krylov exhaustion is detected through a tiny b: a zero tail then ends the
-    // fraction exactly, which the depth rule above already covers.
-    (void)scale;
     MSB_CUDA(cudaMemcpyAsync(I_out, I.p, size_t(nv) * n_w * sizeof(double),
                              I_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
     MSB_CUDA(cudaStreamSynchronize(st));

@@ -85,13 +85,19 @@ __global__ void __launch_bounds__(256) k_mvm_dot(View op, const V* __restrict__ 
     if (st->done) return;
     __shared__ double sm[2 * 32];
     double acc[2] = {0.0, 0.0};
+    DF4 df;
     for (int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < n;
          s += int64_t(gridDim.x) * blockDim.x) {
         const V ps = p[s];
         const V h = op.hx(s, p, ps);
         const V vs = vadd(h, cscale(c0r, c0i, ps));
         v[s] = vs;
-        bil_acc(ps, vs, acc[0], acc[1]);
+        if constexpr (std::is_same<V, float2>::value) bil_acc_df(ps, vs, df);
+        else bil_acc(ps, vs, acc[0], acc[1]);
+    }
+    if constexpr (std::is_same<V, float2>::value) {
+        acc[0] = df_value(df.rh, df.rl);
+        acc[1] = df_value(df.ih, df.il);
     }
     store_partials<2>(acc, sm, part);
 }
@@ -172,12 +178,23 @@ __global__ void __launch_bounds__(256) k_seed_update(V* ring, const V* __restric
     V* __restrict__ rn = ring + int64_t(nxt) * n;
     const double2 a = st->alpha;
     double acc[3] = {0.0, 0.0, 0.0};
+    DF4 df;
     for (int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < n;
          s += int64_t(gridDim.x) * blockDim.x) {
         const V x = vsub(r[s], cscale(a.x, a.y, v[s]));
         rn[s] = x;
-        bil_acc(x, x, acc[0], acc[1]);
-        acc[2] += norm2(x);
+        if constexpr (std::is_same<V, float2>::value) {
+            bil_acc_df(x, x, df);
+            norm_acc_df(x, df);
+        } else {
+            bil_acc(x, x, acc[0], acc[1]);
+            acc[2] += norm2(x);
+        }
+    }
+    if constexpr (std::is_same<V, float2>::value) {
+        acc[0] = df_value(df.rh, df.rl);
+        acc[1] = df_value(df.ih, df.il);
+        acc[2] = df_value(df.nh, df.nl);
     }
     store_partials<3>(acc, sm, part);
 }
@@ -346,13 +363,24 @@ __global__ void __launch_bounds__(256) k_init_vectors(const V* __restrict__ b, V
                                                       V* __restrict__ p, int64_t n, double* part) {
     __shared__ double sm[3 * 32];
     double acc[3] = {0.0, 0.0, 0.0};
+    DF4 df;
     for (int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < n;
          s += int64_t(gridDim.x) * blockDim.x) {
         const V x = b[s];
         ring[s] = x;
         p[s] = x;
-        bil_acc(x, x, acc[0], acc[1]);
-        acc[2] += norm2(x);
+        if constexpr (std::is_same<V, float2>::value) {
+            bil_acc_df(x, x, df);
+            norm_acc_df(x, df);
+        } else {
+            bil_acc(x, x, acc[0], acc[1]);
+            acc[2] += norm2(x);
+        }
+    }
+    if constexpr (std::is_same<V, float2>::value) {
+        acc[0] = df_value(df.rh, df.rl);
+        acc[1] = df_value(df.ih, df.il);
+        acc[2] = df_value(df.nh, df.nl);
     }
     store_partials<3>(acc, sm, part);
 }

@@ -68,10 +68,13 @@ struct HubView {
     double t, U, Uc;
     int core;              // core-hole site, -1: none (plain H)
 
-    __device__ __forceinline__ double diag(int64_t iu, int64_t id) const {
+    // U popc(u & d) - Uc (n_{j,up} + n_{j,dn}), in the vector's precision (no
+    // FP64 work in the FP32 path).
+    template <typename S>
+    __device__ __forceinline__ S diag(int64_t iu, int64_t id) const {
         const uint32_t a = __ldg(sup + iu), b = __ldg(sdn + id);
-        double v = U * double(__popc(a & b));
-        if (core >= 0) v -= Uc * double(((a >> core) & 1u) + ((b >> core) & 1u));
+        S v = S(U) * S(__popc(a & b));
+        if (core >= 0) v -= S(Uc) * S(((a >> core) & 1u) + ((b >> core) & 1u));
         return v;
     }
 
@@ -93,7 +96,7 @@ struct HubView {
             acc = (h & 1) ? vsub(acc, v) : vadd(acc, v);
         }
         // H x = diag * x - t * sum(sign * x_neighbour)
-        return vaxpy(S(-t), acc, vscale(S(diag(iu, id)), xs));
+        return vaxpy(S(-t), acc, vscale(diag<S>(iu, id), xs));
     }
 
     template <typename V>
