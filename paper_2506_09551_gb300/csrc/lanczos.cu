@@ -496,14 +496,44 @@ __global__ void __launch_bounds__(256, 6) k_cf_apply_hub(HubView h, const C* __r
     float dhi = 0.f, dlo = 0.f;
     for (int d = threadIdx.x; d < Ddn; d += blockDim.x) {
         S ax = 0, ay = 0;
-        for (int e = 0; e < nu; ++e) {
-            const C v = Vc[s_uoff[e] + d];
-            const S sg = s_usg[e];
-            ax = fma(sg, v.x, ax);
-            ay = fma(sg, v.y, ay);
+        // up-spin hops: gathers issued four at a time before they are consumed
+        int e = 0;
+        for (; e + 4 <= nu; e += 4) {
+            const C v0 = Vc[s_uoff[e] + d], v1 = Vc[s_uoff[e + 1] + d];
+            const C v2 = Vc[s_uoff[e + 2] + d], v3 = Vc[s_uoff[e + 3] + d];
+            ax = fma(s_usg[e], v0.x, ax);
+            ay = fma(s_usg[e], v0.y, ay);
+            ax = fma(s_usg[e + 1], v1.x, ax);
+            ay = fma(s_usg[e + 1], v1.y, ay);
+            ax = fma(s_usg[e + 2], v2.x, ax);
+            ay = fma(s_usg[e + 2], v2.y, ay);
+            ax = fma(s_usg[e + 3], v3.x, ax);
+            ay = fma(s_usg[e + 3], v3.y, ay);
         }
+        for (; e < nu; ++e) {
+            const C v = Vc[s_uoff[e] + d];
+            ax = fma(s_usg[e], v.x, ax);
+            ay = fma(s_usg[e], v.y, ay);
+        }
+        // down-spin hops: table entries, then row values, four at a time
         const int nd = __ldg(h.ndn + d);
-        for (int e = 0; e < nd; ++e) {
+        e = 0;
+        for (; e + 4 <= nd; e += 4) {
+            const int32_t h0 = __ldg(h.hdn + e * Ddn + d), h1 = __ldg(h.hdn + (e + 1) * Ddn + d);
+            const int32_t h2 = __ldg(h.hdn + (e + 2) * Ddn + d), h3 = __ldg(h.hdn + (e + 3) * Ddn + d);
+            const C v0 = row[h0 >> 1], v1 = row[h1 >> 1], v2 = row[h2 >> 1], v3 = row[h3 >> 1];
+            const S g0 = (h0 & 1) ? S(-1) : S(1), g1 = (h1 & 1) ? S(-1) : S(1);
+            const S g2 = (h2 & 1) ? S(-1) : S(1), g3 = (h3 & 1) ? S(-1) : S(1);
+            ax = fma(g0, v0.x, ax);
+            ay = fma(g0, v0.y, ay);
+            ax = fma(g1, v1.x, ax);
+            ay = fma(g1, v1.y, ay);
+            ax = fma(g2, v2.x, ax);
+            ay = fma(g2, v2.y, ay);
+            ax = fma(g3, v3.x, ax);
+            ay = fma(g3, v3.y, ay);
+        }
+        for (; e < nd; ++e) {
             const int32_t hh = __ldg(h.hdn + e * Ddn + d);
             const C v = row[hh >> 1];
             const S sg = (hh & 1) ? S(-1) : S(1);
