@@ -41,6 +41,8 @@ WORKLOADS = {
     "hubbard-L8-fp64": (workloads.CHAIN8, 0, 1e-10, 1e-10),
 }
 DEFAULT = "hubbard-L12-fp64"
+# random complex-symmetric stress workload: name -> precision, tolerance
+CSR_WORKLOADS = {"random-csr-fp64": (0, 1e-10), "random-csr-mixed": (1, 1e-7)}
 
 # Roofline denominators.  HBM: the measured copy bandwidth of this machine.  FP64:
 # 152 SMs x 2 FP64 FMA per clock x 2 FLOP x 2.07 GHz (nominal 1.25 TFLOP/s).
@@ -209,6 +211,95 @@ def dominant_roofline(stats, prec, peaks):
                  "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}
 
 
+def gpu_arm_csr(args, rank, world):
+    """n = 2^22 random real symmetric matrix, 256 shifts sigma_k + 0.3i: one step =
+    the multi-shift solve of all shifts (solutions stay on the device)."""
+    import torch
+    from paper_2506_09551_gb300 import api, native
+
+    native.load()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    prec, tol = CSR_WORKLOADS[args.workload]
+    wl = workloads.RANDOM_CSR
+    rowptr, col, val = workloads.random_symmetric_csr(wl.n, wl.half_nnz_per_row, wl.diag_range,
+                                                      wl.matrix_seed + rank)
+    b = torch.tensor(workloads.random_complex_rhs(wl.n, wl.rhs_seed + rank), device="cuda")
+    sig = workloads.random_shifts(wl.n_shifts, *wl.shift_range, wl.shift_imag, wl.shift_seed)
+    seed = int(np.argsort(sig.real)[len(sig) // 2])
+    op = api.Operator.csr(rowptr, col, val)
+    lib = native.load()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def step():
+        return op.multishift_solve(b, sig - sig[seed], -sig[seed], tol=tol, maxit=20000, prec=prec,
+                                   allow_status=(native.MSB_EMAXITER,))
+
+    for _ in range(args.warmup):
+        x, per, info, st = step()
+        del x
+    torch.cuda.synchronize()
+    barrier()
+    lib.msb_profile_reset()
+    lib.msb_profile_enable(1)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(None if args.no_clocks else str(local)) as clk:
+        torch.cuda.synchronize()
+        barrier()
+        e0.record(stream)
+        for _ in range(args.steps):
+            x, per, info, st = step()
+        e1.record(stream)
+        e1.synchronize()
+    lib.msb_profile_enable(0)
+    stats = native.profile_read()
+    ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    # end to end: host matrix and right-hand side in, host solutions out
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    if not args.no_e2e:
+        op2 = api.Operator.csr(rowptr, col, val)
+        b2 = torch.tensor(workloads.random_complex_rhs(wl.n, wl.rhs_seed + rank)).pin_memory().to("cuda")
+        x2, *_ = op2.multishift_solve(b2, sig - sig[seed], -sig[seed], tol=tol, maxit=20000, prec=prec,
+                                      allow_status=(native.MSB_EMAXITER,))
+        xh = x2.cpu()
+        del op2, x2, xh
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    top, roof = dominant_roofline(stats, prec, measured_peaks())
+    total_ms = sum(s_["ms"] for s_ in stats)
+    csz = 16 if prec == 0 else 8
+    return {
+        "metric": "shifted solves/s (random complex-symmetric CSR)",
+        "value": world * wl.n_shifts / (ms * 1e-3),
+        "unit": "solves/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "c128" if prec == 0 else "c64 vectors, f64 scalars", "data": "synthetic random CSR",
+        "config": {"workload": args.workload, "n": wl.n, "nnz": int(len(val)), "n_shifts": wl.n_shifts,
+                   "tol": tol, "seed_shift": seed, "l2": "working set larger than L2; no flush needed"},
+        "e2e": {"value": world * wl.n_shifts / e2e_s, "unit": "solves/s",
+                "h2d_bytes_per_step": int(rowptr.nbytes + col.nbytes + val.nbytes + wl.n * 16),
+                "d2h_bytes_per_step": int(wl.n_shifts * wl.n * csz), "seconds": e2e_s},
+        "gpu_launches": int(info["kernel_launches"]),
+        "roofline": roof, "clocks": clk.summary(),
+        "solve": {"iterations": info["iterations"], "n_converged": info["n_converged"],
+                  "max_shift_residual": info["max_shift_residual"], "device_bytes": info["device_bytes"]},
+        "kernels": sorted([{"name": s_["name"], "launches": s_["launches"], "ms": round(s_["ms"], 3),
+                            "share": round(s_["ms"] / total_ms, 4)} for s_ in stats], key=lambda d: -d["ms"]),
+        "cpu_baseline": None,
+    }
+
+
 def gpu_arm(args, rank, world):
     import torch
     from paper_2506_09551_gb300 import api, native
@@ -362,7 +453,7 @@ def main():
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT)
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + sorted(CSR_WORKLOADS), default=DEFAULT)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end map (profiling runs)")
     ap.add_argument("--no-clocks", action="store_true", help="do not sample nvidia-smi (profiling runs)")
@@ -385,6 +476,14 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         dist.init_process_group("nccl")
+    if args.workload in CSR_WORKLOADS:
+        line = gpu_arm_csr(args, rank, world)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
     line = gpu_arm(args, rank, world)
     if rank == 0:
         if not args.no_cpu_baseline and world == 1:
