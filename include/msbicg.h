@@ -292,6 +292,17 @@ void msb_profile_reset(void);
  * array; may be NULL to count) and return how many there are. */
 int msb_profile_read(msb_kernel_stat *out, int max);
 
+/* Maps for several right-hand sides of one model: O2 = c^dag_{j,up}, O1 =
+ * c_{j,up} and the core hole on site j for every j in sites[n_sites] (Eqs. 1-2
+ * per site; the batched workload of one cluster with one right-hand side per
+ * core site).  One ground state; one multi-shift solve per site on that site's
+ * H'; one continued fraction over all n_sites * n_in columns, which share H.
+ * model->core_site is ignored.  I_out: HOST array n_sites x n_in x n_w (site
+ * slowest).  Requires n_sites * n_in <= 65535.  Synchronises `stream`. */
+msb_status msb_rixs_map_sites(const msb_model *model, const msb_map_params *params, const int *sites,
+                              int n_sites, const double *w_in, int n_in, const double *w, int n_w,
+                              double *I_out, msb_solve_info *info, void *stream);
+
 /* Same map with the operators already built and the result left on the
  * device: H = msb_op_create_hubbard(model, 0), Hp = msb_op_create_hubbard(model,
  * 1) of one model (checked); w_in, w are HOST grids (copied in); I_dev is a

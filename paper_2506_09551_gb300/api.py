@@ -185,6 +185,21 @@ def rixs_map_ops(H: Operator, Hp: Operator, params: N.msb_map_params, w_in, w, G
     return I, info.as_dict(), st
 
 
+def rixs_map_sites(m: N.msb_model, params: N.msb_map_params, sites, w_in, w, allow_status=(N.MSB_EMAXITER,)):
+    """Maps of several core sites, I[n_sites, n_in, n_w] (numpy), info dict, status."""
+    sites = np.ascontiguousarray(sites, dtype=np.int32)
+    w_in = np.ascontiguousarray(w_in, dtype=np.float64)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    I = np.zeros((len(sites), len(w_in), len(w)), dtype=np.float64)
+    info = N.msb_solve_info()
+    st = N.load().msb_rixs_map_sites(C.byref(m), C.byref(params), sites.ctypes.data_as(C.POINTER(C.c_int)),
+                                     len(sites), w_in.ctypes.data_as(C.POINTER(C.c_double)), len(w_in),
+                                     w.ctypes.data_as(C.POINTER(C.c_double)), len(w),
+                                     I.ctypes.data_as(C.POINTER(C.c_double)), C.byref(info), _stream())
+    N.check(st, allow=allow_status)
+    return I, info.as_dict(), st
+
+
 def rixs_map(m: N.msb_model, params: N.msb_map_params, w_in, w, G: torch.Tensor | None = None, E_G: float = 0.0,
              allow_status=(N.MSB_EMAXITER,)):
     """The RIXS map I[n_in, n_w] (numpy), the solve info (dict) and the status."""

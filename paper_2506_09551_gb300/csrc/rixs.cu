@@ -122,6 +122,85 @@ static void apply_sector_map(const msb_model& m, int site, bool create, const vo
 // ---------------------------------------------------------------------------
 // The map
 // ---------------------------------------------------------------------------
+// Steps 3-5 of the map for one core site (m.core_site): E = O2|G>, the
+// multi-shift solve on H' of that site, and phi_k = O1 Psi_k written to Phi
+// (n_in vectors of the ground sector, precision of prm).  Returns the solve status.
+static msb_status solve_site(msb_op* opHp, const msb_op* opH, const msb_model& m, const msb_map_params& prm,
+                             const double* G, double E_G, const double* w_in, int n_in, char* Phi,
+                             msb_solve_info& info, cudaStream_t st, int64_t& launches) {
+    const int64_t D = opH->dim, Dp = opHp->dim, Ddn = opH->hub.Ddn;
+    const size_t csz = prm.precision == MSB_FP64 ? sizeof(double2) : sizeof(float2);
+    DevBuf<char> Ebuf(size_t(Dp) * csz);
+    {
+        auto map = cdag_rowmap(m.L, m.n_up, m.core_site);
+        if (prm.precision == MSB_FP64)
+            launch_rowmap(G, (double2*)Ebuf.p, map, Ddn, D, Dp, 1, st, launches);
+        else
+            launch_rowmap(G, (float2*)Ebuf.p, map, Ddn, D, Dp, 1, st, launches);
+    }
+    // rows of the intermediate sector that O1 reads (site j up-occupied)
+    const auto up_hi = sector_states(m.L, m.n_up + 1);
+    std::vector<int32_t> rows;
+    std::vector<int32_t> pos(up_hi.size(), -1);
+    for (size_t r = 0; r < up_hi.size(); ++r)
+        if ((up_hi[r] >> m.core_site) & 1u) { pos[r] = int32_t(rows.size()); rows.push_back(int32_t(r)); }
+    DevBuf<int32_t> drows(rows.size());
+    drows.upload(rows.data(), rows.size(), st);
+    const int64_t n_out = int64_t(rows.size()) * Ddn;
+    // seed and shifts
+    int s0 = prm.seed_index;
+    if (s0 < 0) {
+        s0 = 0;
+        for (int k = 1; k < n_in; ++k) if (std::fabs(w_in[k]) < std::fabs(w_in[s0])) s0 = k;
+    }
+    MSB_REQUIRE(s0 < n_in, "seed_index out of range");
+    SolveProblem pr;
+    pr.n = Dp;
+    pr.ns = n_in;
+    pr.b = Ebuf.p;
+    pr.n_out = n_out;
+    pr.rows = drows.p;
+    pr.rowlen = Ddn;
+    pr.c0 = make_double2(-E_G - w_in[s0], -prm.Gamma);
+    pr.tol = prm.solve_tol;
+    pr.maxit = prm.maxit;
+    pr.block = pick_block(prm.block, prm.precision);
+    pr.prec = prm.precision;
+    pr.shifts.resize(n_in);
+    for (int k = 0; k < n_in; ++k) pr.shifts[k] = make_double2(w_in[k] - w_in[s0], 0.0);
+    DevBuf<char> Xsub(size_t(n_in) * n_out * csz);
+    pr.x = Xsub.p;
+    SolveResult sr;
+    multishift_solve(opHp, pr, sr, st);
+    MSB_CUDA(cudaStreamSynchronize(st));
+    launches += sr.launches;
+    info.iterations = std::max(info.iterations, sr.iterations);
+    info.n_converged += sr.n_converged;
+    info.flushes += sr.flushes;
+    info.seed_residual = std::max(info.seed_residual, sr.seed_residual);
+    for (double r : sr.resid) info.max_shift_residual = std::max(info.max_shift_residual, r);
+    info.matvecs += sr.iterations;
+    if (sr.status != MSB_OK && sr.status != MSB_EMAXITER) fail(sr.status, "multi-shift solve failed");
+    Ebuf.release();
+    // phi_k = O1 Psi_k from the carried rows
+    std::vector<int32_t> omap(opH->hub.Dup, -1);
+    {
+        const auto up_lo = sector_states(m.L, m.n_up);
+        auto rhi = rank_table(up_hi, m.L);
+        for (size_t r = 0; r < up_lo.size(); ++r) {
+            const uint32_t u = up_lo[r];
+            if ((u >> m.core_site) & 1u) continue;
+            const int32_t src = pos[rhi[u | (1u << m.core_site)]];
+            omap[r] = (src << 1) | jw_sign_below(u, m.core_site);
+        }
+    }
+    if (prm.precision == MSB_FP64)
+        launch_rowmap((const double2*)Xsub.p, (double2*)Phi, omap, Ddn, n_out, D, n_in, st, launches);
+    else
+        launch_rowmap((const float2*)Xsub.p, (float2*)Phi, omap, Ddn, n_out, D, n_in, st, launches);
+    return sr.status;
+}
+
 void rixs_map_core(msb_op* opH, msb_op* opHp, const msb_model& m, const msb_map_params& prm, const double* G_in,
                    double E_G_in, const double* w_in, int n_in, const double* w, int n_w, double* I_out, bool I_dev,
                    msb_solve_info& info, cudaStream_t st, int64_t launches_so_far);
@@ -160,7 +239,7 @@ void rixs_map_core(msb_op* opH_, msb_op* opHp_, const msb_model& m, const msb_ma
     int64_t launches = launches_so_far;
     struct { msb_op* get() const { return p; } msb_op* operator->() const { return p; } msb_op* p; } opH{opH_},
         opHp{opHp_};
-    const int64_t D = opH->dim, Dp = opHp->dim, Ddn = opH->hub.Ddn;
+    const int64_t D = opH->dim;
 
     // ground state
     auto t0 = std::chrono::steady_clock::now();
@@ -181,85 +260,11 @@ void rixs_map_core(msb_op* opH_, msb_op* opHp_, const msb_model& m, const msb_ma
     info.E_G = E_G;
     info.seconds_ground_state = secs(t0);
 
-    // E = O2 |G>
+    // E = O2 |G>, the multi-shift solve, phi = O1 Psi
     t0 = std::chrono::steady_clock::now();
     const size_t csz = prm.precision == MSB_FP64 ? sizeof(double2) : sizeof(float2);
-    DevBuf<char> Ebuf(size_t(Dp) * csz);
-    {
-        auto map = cdag_rowmap(m.L, m.n_up, m.core_site);
-        if (prm.precision == MSB_FP64)
-            launch_rowmap(G, (double2*)Ebuf.p, map, Ddn, D, Dp, 1, st, launches);
-        else
-            launch_rowmap(G, (float2*)Ebuf.p, map, Ddn, D, Dp, 1, st, launches);
-    }
-
-    // rows of the intermediate sector that O1 reads (site j up-occupied)
-    const auto up_hi = sector_states(m.L, m.n_up + 1);
-    std::vector<int32_t> rows;
-    std::vector<int32_t> pos(up_hi.size(), -1);
-    for (size_t r = 0; r < up_hi.size(); ++r)
-        if ((up_hi[r] >> m.core_site) & 1u) { pos[r] = int32_t(rows.size()); rows.push_back(int32_t(r)); }
-    DevBuf<int32_t> drows(rows.size());
-    drows.upload(rows.data(), rows.size(), st);
-    const int64_t n_out = int64_t(rows.size()) * Ddn;
-
-    // seed and shifts
-    int s0 = prm.seed_index;
-    if (s0 < 0) {
-        s0 = 0;
-        for (int k = 1; k < n_in; ++k) if (std::fabs(w_in[k]) < std::fabs(w_in[s0])) s0 = k;
-    }
-    MSB_REQUIRE(s0 < n_in, "seed_index out of range");
-    SolveProblem pr;
-    pr.n = Dp;
-    pr.ns = n_in;
-    pr.b = Ebuf.p;
-    pr.n_out = n_out;
-    pr.rows = drows.p;
-    pr.rowlen = Ddn;
-    pr.c0 = make_double2(-E_G - w_in[s0], -prm.Gamma);
-    pr.tol = prm.solve_tol;
-    pr.maxit = prm.maxit;
-    pr.block = pick_block(prm.block, prm.precision);
-    pr.prec = prm.precision;
-    pr.shifts.resize(n_in);
-    for (int k = 0; k < n_in; ++k) pr.shifts[k] = make_double2(w_in[k] - w_in[s0], 0.0);
-    DevBuf<char> Xsub(size_t(n_in) * n_out * csz);
-    pr.x = Xsub.p;
-    SolveResult sr;
-    multishift_solve(opHp.get(), pr, sr, st);
-    MSB_CUDA(cudaStreamSynchronize(st));
-    launches += sr.launches;
-    info.iterations = sr.iterations;
-    info.n_converged = sr.n_converged;
-    info.flushes = sr.flushes;
-    info.seed_residual = sr.seed_residual;
-    double mx = 0;
-    for (double r : sr.resid) mx = std::max(mx, r);
-    info.max_shift_residual = mx;
-    info.matvecs += sr.iterations;
-    if (sr.status != MSB_OK && sr.status != MSB_EMAXITER) fail(sr.status, "multi-shift solve failed");
-    Ebuf.release();
-
-    // phi_k = O1 Psi_k from the carried rows
-    std::vector<int32_t> omap(opH->hub.Dup, -1);
-    {
-        const auto up_lo = sector_states(m.L, m.n_up);
-        auto rhi = rank_table(up_hi, m.L);
-        for (size_t r = 0; r < up_lo.size(); ++r) {
-            const uint32_t u = up_lo[r];
-            if ((u >> m.core_site) & 1u) continue;
-            const int32_t src = pos[rhi[u | (1u << m.core_site)]];
-            omap[r] = (src << 1) | jw_sign_below(u, m.core_site);
-        }
-    }
     DevBuf<char> Phi(size_t(n_in) * D * csz);
-    if (prm.precision == MSB_FP64)
-        launch_rowmap((const double2*)Xsub.p, (double2*)Phi.p, omap, Ddn, n_out, D, n_in, st, launches);
-    else
-        launch_rowmap((const float2*)Xsub.p, (float2*)Phi.p, omap, Ddn, n_out, D, n_in, st, launches);
-    Xsub.release();
-    drows.release();
+    const msb_status sst = solve_site(opHp.get(), opH.get(), m, prm, G, E_G, w_in, n_in, Phi.p, info, st, launches);
     info.seconds_solve = secs(t0);
 
     // second step
@@ -276,7 +281,7 @@ void rixs_map_core(msb_op* opH_, msb_op* opHp_, const msb_model& m, const msb_ma
     info.seconds_second_step = secs(t0);
     info.seconds_total = secs(t_start);
     info.kernel_launches = launches;
-    if (sr.status == MSB_EMAXITER) fail(MSB_EMAXITER, "some incident energies did not converge (map written)");
+    if (sst == MSB_EMAXITER) fail(MSB_EMAXITER, "some incident energies did not converge (map written)");
 }
 
 }  // namespace msb
@@ -298,6 +303,76 @@ extern "C" msb_status msb_apply_c_up(const msb_model* model, int site, const voi
         msb::apply_sector_map(*model, site, false, x, y, nvec, prec, (cudaStream_t)stream);
     });
 }
+
+namespace msb {
+
+// Maps of several core sites of one model (one right-hand side O2 = c^dag_{j,up}
+// per site): one ground state, one solve per site on its own H', then one
+// continued fraction over all sites' columns, since H is the same for all.
+static void rixs_map_sites_impl(const msb_model& m, const msb_map_params& prm, const int* sites, int n_sites,
+                                const double* w_in, int n_in, const double* w, int n_w, double* I_out,
+                                msb_solve_info& info, cudaStream_t st) {
+    validate_model(m);
+    MSB_REQUIRE(sites != nullptr && n_sites >= 1, "need at least one site");
+    MSB_REQUIRE(n_in >= 1 && n_in <= kMaxShifts && int64_t(n_sites) * n_in <= 65535,
+                "n_sites * n_in must be at most 65535 (and n_in at most 4096)");
+    MSB_REQUIRE(m.n_up + 1 <= m.L, "the intermediate sector needs n_up + 1 <= L");
+    MSB_REQUIRE(w_in && w && I_out && n_w >= 1, "NULL argument");
+    MSB_REQUIRE(prm.Gamma > 0 && prm.eta > 0, "Gamma and eta must be > 0");
+    for (int i = 0; i < n_sites; ++i) MSB_REQUIRE(sites[i] >= 0 && sites[i] < m.L, "site out of range");
+    const auto t_start = std::chrono::steady_clock::now();
+    auto secs = [](std::chrono::steady_clock::time_point a) {
+        return std::chrono::duration<double>(std::chrono::steady_clock::now() - a).count();
+    };
+    int64_t launches = 0;
+    msb_op* a = nullptr;
+    msb_status s1 = msb_op_create_hubbard(&m, 0, &a);
+    if (s1 != MSB_OK) fail(s1, msb_last_error());
+    std::unique_ptr<msb_op> opH(a);
+    const int64_t D = opH->dim;
+    auto t0 = std::chrono::steady_clock::now();
+    DevBuf<double> g(D);
+    GroundResult gr;
+    ground_state(opH.get(), prm.gs_tol, prm.gs_maxit, nullptr, g.p, gr, st);
+    if (gr.status != MSB_OK) fail(gr.status, "ground state: tolerance not reached");
+    info.E_G = gr.E;
+    info.gs_residual = gr.residual;
+    info.matvecs += gr.matvecs;
+    launches += gr.launches;
+    info.seconds_ground_state = secs(t0);
+    t0 = std::chrono::steady_clock::now();
+    const size_t csz = prm.precision == MSB_FP64 ? sizeof(double2) : sizeof(float2);
+    DevBuf<char> Phi(size_t(n_sites) * n_in * D * csz);
+    bool maxit_hit = false;
+    for (int i = 0; i < n_sites; ++i) {
+        msb_model mj = m;
+        mj.core_site = sites[i];
+        msb_op* b = nullptr;
+        s1 = msb_op_create_hubbard(&mj, 1, &b);
+        if (s1 != MSB_OK) fail(s1, msb_last_error());
+        std::unique_ptr<msb_op> opHp(b);
+        const msb_status sst = solve_site(opHp.get(), opH.get(), mj, prm, g.p, gr.E, w_in, n_in,
+                                          Phi.p + size_t(i) * n_in * D * csz, info, st, launches);
+        maxit_hit |= sst == MSB_EMAXITER;
+    }
+    info.seconds_solve = secs(t0);
+    t0 = std::chrono::steady_clock::now();
+    CFResult cr;
+    continued_fraction(opH.get(), Phi.p, n_sites * n_in, gr.E, w, n_w, prm.eta, prm.cf_tol, prm.cf_check,
+                       prm.cf_maxdepth, prm.precision, I_out, cr, st, false);
+    launches += cr.launches;
+    info.matvecs += cr.matvecs;
+    int dmax = 0, dmin = 1 << 30;
+    for (int d : cr.depth) { dmax = std::max(dmax, d); dmin = std::min(dmin, d); }
+    info.cf_depth_max = dmax;
+    info.cf_depth_min = dmin;
+    info.seconds_second_step = secs(t0);
+    info.seconds_total = secs(t_start);
+    info.kernel_launches = launches;
+    if (maxit_hit) fail(MSB_EMAXITER, "some incident energies did not converge (maps written)");
+}
+
+}  // namespace msb
 
 static bool same_model(const msb_model& a, const msb_model& b) {
     return a.L == b.L && a.n_up == b.n_up && a.n_dn == b.n_dn && a.periodic == b.periodic && a.t == b.t &&
@@ -322,6 +397,26 @@ extern "C" msb_status msb_rixs_map_ops(msb_op* H, msb_op* Hp, const msb_map_para
             ~Fill() { if (dst) { src->device_bytes = msb::g_alloc_bytes; *dst = *src; } }
         } fill{info, &local};
         msb::rixs_map_core(H, Hp, H->model, *params, G, E_G, w_in, n_in, w, n_w, I_dev, true, local, scope.s, 0);
+        scope.finish();
+        msb::prof_collect();
+    });
+}
+
+extern "C" msb_status msb_rixs_map_sites(const msb_model* model, const msb_map_params* params, const int* sites,
+                                         int n_sites, const double* w_in, int n_in, const double* w, int n_w,
+                                         double* I_out, msb_solve_info* info, void* stream) {
+    if (info) *info = msb_solve_info{};
+    return msb::guard("msb_rixs_map_sites", [&] {
+        msb::require_device();
+        MSB_REQUIRE(model != nullptr && params != nullptr, "NULL argument");
+        msb::g_alloc_bytes = 0;
+        msb_solve_info local{};
+        msb::StreamScope scope((cudaStream_t)stream);
+        struct Fill {
+            msb_solve_info* dst; msb_solve_info* src;
+            ~Fill() { if (dst) { src->device_bytes = msb::g_alloc_bytes; *dst = *src; } }
+        } fill{info, &local};
+        msb::rixs_map_sites_impl(*model, *params, sites, n_sites, w_in, n_in, w, n_w, I_out, local, scope.s);
         scope.finish();
         msb::prof_collect();
     });

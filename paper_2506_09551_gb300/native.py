@@ -82,6 +82,8 @@ SIGNATURES = {
                           C.POINTER(msb_solve_info), _P]),
     "msb_rixs_map_ops": (_I, [_P, _P, C.POINTER(msb_map_params), _P, _D, _PD, _I, _PD, _I, _P,
                               C.POINTER(msb_solve_info), _P]),
+    "msb_rixs_map_sites": (_I, [C.POINTER(msb_model), C.POINTER(msb_map_params), C.POINTER(C.c_int), _I, _PD, _I,
+                                _PD, _I, _PD, C.POINTER(msb_solve_info), _P]),
     "msb_profile_enable": (None, [_I]),
     "msb_profile_reset": (None, []),
     "msb_profile_read": (_I, [C.POINTER(msb_kernel_stat), _I]),

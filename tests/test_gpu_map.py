@@ -126,3 +126,21 @@ def test_chain12_sampled_rows(cuda):
         I_ref, _ = spectrum.lanczos_cf(om.H, om.O1 @ X[0], E_G, wl.w, wl.eta, cf_tol=1e-12)
         err = np.linalg.norm(I[k] - I_ref) / np.linalg.norm(I_ref)
         assert err <= 1e-8, (k, err)
+
+
+def test_map_sites_batched_right_hand_sides(cuda, chain8_oracle):
+    """One call for every core site of the L = 8 ring (the batched workload's shape):
+    each site's map equals the single-site call, all sites agree by translation
+    invariance, and site 0 matches the oracle."""
+    from paper_2506_09551_gb300 import api
+    wl, ref = chain8_oracle
+    m = api.model(wl.L, wl.n_up, wl.n_dn)
+    p = _params(api, solve_tol=1e-10, cf_tol=1e-10)
+    sites = list(range(wl.L))
+    I, info, st = api.rixs_map_sites(m, p, sites, wl.w_in, wl.w)
+    assert st == 0 and I.shape == (wl.L, wl.n_in, wl.n_w)
+    assert orixs.relative_l2(I[0], ref.I) <= 1e-8
+    single, _, _ = api.rixs_map(api.model(wl.L, wl.n_up, wl.n_dn, core_site=3), p, wl.w_in, wl.w)
+    assert orixs.relative_l2(I[3], single) <= 1e-9
+    for j in sites[1:]:
+        assert orixs.relative_l2(I[j], I[0]) <= 1e-8, j
