@@ -200,17 +200,28 @@ def run_cpu_baseline(name: str) -> dict:
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
-def dominant_roofline(stats, prec, peaks):
+def measured_traffic(workload, kernel, alg_bytes_per_launch):
+    """DRAM bytes per launch scaled from an ncu capture of the same kernel (None if none)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
+            rec = json.load(f)[workload][kernel]
+    except (OSError, KeyError, ValueError):
+        return None
+    return rec["dram_bytes"] / rec["alg_bytes"] * alg_bytes_per_launch
+
+
+def dominant_roofline(stats, prec, peaks, workload=None):
     top = max(stats, key=lambda s: s["ms"])
     avg_ms = top["ms"] / top["launches"]
+    traffic = measured_traffic(workload, top["name"], top["alg_bytes"] / top["launches"])
     if prec == 0:
         achieved = top["alg_flops"] / top["launches"] / (avg_ms * 1e-3) / 1e12
         return top, {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "kernel": top["name"],
+                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic, "kernel": top["name"],
                      "peak_source": "derived FP64: 152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz"}
     achieved = top["alg_bytes"] / top["launches"] / (avg_ms * 1e-3) / 1e9
     return top, {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                 "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": top["name"],
+                 "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "kernel": top["name"],
                  "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}
 
 
@@ -394,7 +405,7 @@ def gpu_arm(args, rank, world):
             if not sites and np.max(np.abs(I_host)) > 0 else None)
 
     peaks = measured_peaks()
-    top, roof = dominant_roofline(stats, prec, peaks)
+    top, roof = dominant_roofline(stats, prec, peaks, args.workload)
     total_ms = sum(s["ms"] for s in stats)
     apply_cls = [s for s in stats if s["name"] in ("cf_apply", "seed_mvm", "h_apply")]
     h_gbs = (sum(s["alg_bytes"] for s in apply_cls) / (sum(s["ms"] for s in apply_cls) * 1e-3) / 1e9
