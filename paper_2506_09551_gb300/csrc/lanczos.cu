@@ -566,6 +566,120 @@ __global__ void __launch_bounds__(256, 6) k_cf_apply_hub(HubView h, const C* __r
     if (threadIdx.x == 0) part[int64_t(blockIdx.y) * gridDim.x + blockIdx.x] = acc[0];
 }
 
+// FP32 pass A with two adjacent elements per thread: the up-spin gathers, the
+// V_{k-1} loads and the W stores move 16 bytes (two complex floats) at a time,
+// and the down-spin table is read as 16-bit entries, two per 32-bit load.
+// Needs an even Ddn (rows start on 16-byte boundaries) and Ddn < 32768.
+__global__ void __launch_bounds__(256, 6) k_cf_apply_hub_f2x2(HubView h, const float2* __restrict__ Vk,
+                                                              const float2* __restrict__ Vkm1, float2* __restrict__ W,
+                                                              int64_t ld, const int* __restrict__ cols, CFCoef cf,
+                                                              double* part, int L) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    float2* row = reinterpret_cast<float2*>(sm_raw);                // Ddn values of row u
+    float* lut = reinterpret_cast<float*>(row + h.Ddn);             // 3 (L + 1) diagonal values * sig
+    __shared__ int s_uoff[kMaxHops];
+    __shared__ float s_usg[kMaxHops];
+    __shared__ double red[32];
+    const int c = cols[blockIdx.y];
+    const int u = blockIdx.x;
+    const int Ddn = int(h.Ddn);
+    const int half = Ddn >> 1;
+    const float2* __restrict__ Vc = Vk + int64_t(c) * ld;
+    const float4* __restrict__ Pc4 = reinterpret_cast<const float4*>(Vkm1 + int64_t(c) * ld);
+    float4* __restrict__ Wc4 = reinterpret_cast<float4*>(W + int64_t(c) * ld);
+    const int rbase = u * Ddn;                      // even
+    const double sig = cf.sig[c], cB = cf.cB[c];
+    const bool has_prev = cB != 0.0;
+    const uint32_t su = __ldg(h.sup + u);
+    const int nu = __ldg(h.nup + u);
+    {
+        const float4* src = reinterpret_cast<const float4*>(Vc + rbase);
+        float4* dst = reinterpret_cast<float4*>(row);
+        for (int i = threadIdx.x; i < half; i += blockDim.x) dst[i] = src[i];
+    }
+    for (int i = threadIdx.x; i < 3 * (L + 1); i += blockDim.x) {
+        const int p = i % (L + 1), nb = i / (L + 1);
+        lut[i] = float(sig * (h.U * double(p) - h.Uc * double(nb)));
+    }
+    if (threadIdx.x < nu) {
+        const int32_t ent = __ldg(h.hup + int64_t(threadIdx.x) * h.Dup + u);
+        s_uoff[threadIdx.x] = ((ent >> 1) * Ddn) >> 1;           // in float4 units
+        s_usg[threadIdx.x] = (ent & 1) ? -1.f : 1.f;
+    }
+    __syncthreads();
+    const int core = h.core;
+    const int ubits = core >= 0 ? int((su >> core) & 1u) : 0;
+    const float mt = float(-h.t * sig);
+    const float mcB = float(-cB);
+    const float4* __restrict__ Vc4 = reinterpret_cast<const float4*>(Vc);
+    const uint32_t* __restrict__ t32 = reinterpret_cast<const uint32_t*>(h.hdn16);
+    const uint16_t* __restrict__ n16 = reinterpret_cast<const uint16_t*>(h.ndn);
+    const uint2* __restrict__ sd2 = reinterpret_cast<const uint2*>(h.sdn);
+    float dhi = 0.f, dlo = 0.f;
+    for (int q = threadIdx.x; q < half; q += blockDim.x) {      // elements d0 = 2q, d1 = 2q + 1
+        float a0x = 0.f, a0y = 0.f, a1x = 0.f, a1y = 0.f;
+        int e = 0;
+        for (; e + 2 <= nu; e += 2) {
+            const float4 v = Vc4[s_uoff[e] + q], w4 = Vc4[s_uoff[e + 1] + q];
+            const float g = s_usg[e], g2 = s_usg[e + 1];
+            a0x = fmaf(g, v.x, a0x); a0y = fmaf(g, v.y, a0y);
+            a1x = fmaf(g, v.z, a1x); a1y = fmaf(g, v.w, a1y);
+            a0x = fmaf(g2, w4.x, a0x); a0y = fmaf(g2, w4.y, a0y);
+            a1x = fmaf(g2, w4.z, a1x); a1y = fmaf(g2, w4.w, a1y);
+        }
+        if (e < nu) {
+            const float4 v = Vc4[s_uoff[e] + q];
+            const float g = s_usg[e];
+            a0x = fmaf(g, v.x, a0x); a0y = fmaf(g, v.y, a0y);
+            a1x = fmaf(g, v.z, a1x); a1y = fmaf(g, v.w, a1y);
+        }
+        const uint32_t nn = __ldg(n16 + q);
+        const int nd0 = int(nn & 0xFFu), nd1 = int(nn >> 8);
+        const int ndm = nd0 > nd1 ? nd0 : nd1;
+        for (int k = 0; k < ndm; ++k) {
+            const uint32_t tt = __ldg(t32 + (k * Ddn >> 1) + q);
+            if (k < nd0) {
+                const uint32_t h0 = tt & 0xFFFFu;
+                const float2 v = row[h0 >> 1];
+                const float g = (h0 & 1u) ? -1.f : 1.f;
+                a0x = fmaf(g, v.x, a0x); a0y = fmaf(g, v.y, a0y);
+            }
+            if (k < nd1) {
+                const uint32_t h1 = tt >> 16;
+                const float2 v = row[h1 >> 1];
+                const float g = (h1 & 1u) ? -1.f : 1.f;
+                a1x = fmaf(g, v.x, a1x); a1y = fmaf(g, v.y, a1y);
+            }
+        }
+        const uint2 sd = __ldg(sd2 + q);
+        const int nb0 = core >= 0 ? ubits + int((sd.x >> core) & 1u) : 0;
+        const int nb1 = core >= 0 ? ubits + int((sd.y >> core) & 1u) : 0;
+        const float dg0 = lut[__popc(su & sd.x) + nb0 * (L + 1)];
+        const float dg1 = lut[__popc(su & sd.y) + nb1 * (L + 1)];
+        const float2 x0 = row[2 * q], x1 = row[2 * q + 1];
+        float4 wv;
+        wv.x = fmaf(mt, a0x, dg0 * x0.x);
+        wv.y = fmaf(mt, a0y, dg0 * x0.y);
+        wv.z = fmaf(mt, a1x, dg1 * x1.x);
+        wv.w = fmaf(mt, a1y, dg1 * x1.y);
+        if (has_prev) {
+            const float4 y = __ldcs(Pc4 + (rbase >> 1) + q);
+            wv.x = fmaf(mcB, y.x, wv.x);
+            wv.y = fmaf(mcB, y.y, wv.y);
+            wv.z = fmaf(mcB, y.z, wv.z);
+            wv.w = fmaf(mcB, y.w, wv.w);
+        }
+        __stcs(Wc4 + (rbase >> 1) + q, wv);
+        df_add_prod(dhi, dlo, x0.x, wv.x);
+        df_add_prod(dhi, dlo, x0.y, wv.y);
+        df_add_prod(dhi, dlo, x1.x, wv.z);
+        df_add_prod(dhi, dlo, x1.y, wv.w);
+    }
+    double acc[1] = {df_value(dhi, dlo)};
+    block_sum<1>(acc, red);
+    if (threadIdx.x == 0) part[int64_t(blockIdx.y) * gridDim.x + blockIdx.x] = acc[0];
+}
+
 // Pass A for any operator view (CSR): flat grid over elements.
 template <class View, typename C>
 __global__ void __launch_bounds__(256) k_cf_apply_gen(View op, const C* __restrict__ Vk, const C* __restrict__ Vkm1,
@@ -739,7 +853,7 @@ static void cf_impl(const msb_op* op, const View& view, int64_t n, const void* p
     const int grid = grid_for(ld / per, 256, 4);
     int64_t hub_smem = 0;
     int L = 0;
-    bool rows = false;
+    bool rows = false, pair = false;
     int nblkA = grid;
     if constexpr (hub) {
         L = op->model.L;
@@ -749,6 +863,10 @@ static void cf_impl(const msb_op* op, const View& view, int64_t n, const void* p
             nblkA = int(view.Dup);
             MSB_CUDA(cudaFuncSetAttribute(k_cf_apply_hub<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           int(hub_smem)));
+            pair = std::is_same<C, float2>::value && view.Ddn % 2 == 0 && view.hdn16 != nullptr;
+            if (pair)
+                MSB_CUDA(cudaFuncSetAttribute(k_cf_apply_hub_f2x2, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              int(hub_smem)));
         }
     }
     DevBuf<C> Q(3 * size_t(nv) * ld);
@@ -783,7 +901,12 @@ static void cf_impl(const msb_op* op, const View& view, int64_t n, const void* p
                          nact * (op->hx_flops() + 8.0 * n));
             bool done_hub = false;
             if constexpr (hub) {
-                if (rows) {
+                if (rows && pair) {
+                    k_cf_apply_hub_f2x2<<<dim3(unsigned(nblkA), nact), 256, hub_smem, st>>>(
+                        view, reinterpret_cast<const float2*>(vk), reinterpret_cast<const float2*>(vkm1),
+                        reinterpret_cast<float2*>(wv), ld, cols.p, cf, part.p, L);
+                    done_hub = true;
+                } else if (rows) {
                     k_cf_apply_hub<C><<<dim3(unsigned(nblkA), nact), 256, hub_smem, st>>>(view, vk, vkm1, wv, ld,
                                                                                           cols.p, cf, part.p, L);
                     done_hub = true;

@@ -29,6 +29,12 @@ static void build_hubbard(msb_op* op, const msb_model& m, int intermediate) {
     op->ndn.alloc(cd.size()); op->ndn.upload(cd.data(), cd.size());
     op->sup.alloc(op->host_up.size()); op->sup.upload(op->host_up.data(), op->host_up.size());
     op->sdn.alloc(op->host_dn.size()); op->sdn.upload(op->host_dn.data(), op->host_dn.size());
+    if (op->host_dn.size() < 32768) {
+        std::vector<uint16_t> t16(td.size());
+        for (size_t i = 0; i < td.size(); ++i) t16[i] = td[i] < 0 ? uint16_t(0xFFFF) : uint16_t(td[i]);
+        op->hdn16.alloc(t16.size());
+        op->hdn16.upload(t16.data(), t16.size());
+    }
     MSB_CUDA(cudaDeviceSynchronize());
     HubView& h = op->hub;
     h.Dup = int64_t(op->host_up.size());
@@ -37,6 +43,7 @@ static void build_hubbard(msb_op* op, const msb_model& m, int intermediate) {
     h.Wdn = Wd;
     h.hup = op->hup.p; h.hdn = op->hdn.p;
     h.nup = op->nup.p; h.ndn = op->ndn.p;
+    h.hdn16 = op->hdn16.p;
     h.sup = op->sup.p; h.sdn = op->sdn.p;
     h.t = m.t; h.U = m.U; h.Uc = m.Uc;
     h.core = intermediate ? m.core_site : -1;

@@ -63,6 +63,7 @@ struct HubView {
     const int32_t* hdn;
     const uint8_t* nup;
     const uint8_t* ndn;
+    const uint16_t* hdn16;  // [slot][state] down-spin table with 16-bit entries (Ddn < 32768), else null
     const uint32_t* sup;   // occupation strings, rank order
     const uint32_t* sdn;
     double t, U, Uc;
@@ -144,6 +145,7 @@ struct msb_op {
     int sec_up = 0, sec_dn = 0;  // electrons of this operator's sector
     msb::DevBuf<int32_t> hup, hdn;
     msb::DevBuf<uint8_t> nup, ndn;
+    msb::DevBuf<uint16_t> hdn16;
     msb::DevBuf<uint32_t> sup, sdn;
     std::vector<uint32_t> host_up, host_dn;
     msb::HubView hub{};

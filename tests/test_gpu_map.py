@@ -144,3 +144,23 @@ def test_map_sites_batched_right_hand_sides(cuda, chain8_oracle):
     assert orixs.relative_l2(I[3], single) <= 1e-9
     for j in sites[1:]:
         assert orixs.relative_l2(I[j], I[0]) <= 1e-8, j
+
+
+@pytest.mark.parametrize("L,nu,nd,periodic", [(8, 4, 4, True), (7, 3, 3, False), (10, 5, 5, True)])
+def test_continued_fraction_fp32(cuda, L, nu, nd, periodic):
+    """FP32 second step vs the oracle's FP64 fraction on the same phi (even D_dn uses the
+    two-elements-per-thread kernel, odd D_dn the general one)."""
+    from paper_2506_09551_gb300 import api
+    om = hubbard.RixsModel(L, nu, nd, 1.0, 8.0, 4.0, 0, periodic)
+    E_G, G, _ = solvers.ground_state(om.H, workloads.lanczos_start(om.H.shape[0], 1))
+    n = om.Hp.shape[0]
+    A = (om.Hp - (E_G + 0.3j) * sp.identity(n)).tocsr()
+    X, _ = solvers.solve_shifted(A, om.O2 @ G, np.array([-2.0, 0.0, 4.0]), tol=1e-12)
+    phi = (om.O1 @ X.T).T
+    w = np.linspace(-1, 10, 60)
+    op = api.Operator.hubbard(api.model(L, nu, nd, periodic=periodic))
+    I, depth = op.continued_fraction(torch.tensor(phi, dtype=torch.complex64, device="cuda"), E_G, w, 0.1,
+                                     cf_tol=1e-7)
+    for k in range(3):
+        ref, _ = spectrum.lanczos_cf(om.H, phi[k], E_G, w, 0.1)
+        assert np.max(np.abs(I[k] - ref)) <= 1e-4 * np.max(ref), k
