@@ -156,7 +156,7 @@ def test_continued_fraction_fp32(cuda, L, nu, nd, periodic):
     n = om.Hp.shape[0]
     A = (om.Hp - (E_G + 0.3j) * sp.identity(n)).tocsr()
     X, _ = solvers.solve_shifted(A, om.O2 @ G, np.array([-2.0, 0.0, 4.0]), tol=1e-12)
-    phi = (om.O1 @ X.T).T
+    phi = np.ascontiguousarray((om.O1 @ X.T).T)
     w = np.linspace(-1, 10, 60)
     op = api.Operator.hubbard(api.model(L, nu, nd, periodic=periodic))
     I, depth = op.continued_fraction(torch.tensor(phi, dtype=torch.complex64, device="cuda"), E_G, w, 0.1,
