@@ -566,6 +566,145 @@ __global__ void __launch_bounds__(256, 6) k_cf_apply_hub(HubView h, const C* __r
     if (threadIdx.x == 0) part[int64_t(blockIdx.y) * gridDim.x + blockIdx.x] = acc[0];
 }
 
+// ---------------------------------------------------------------------------
+// FP64 pass A with the hop sums accumulated exactly in 64-bit fixed point.
+//
+// On this GPU the FP64 pipe issues a small fraction of the integer rate, and
+// 2 of every 2.5 FP64 operations of the plain kernel are the +-1 hop terms.
+// Here every component of V_k is bounded by ||V_k|| = 1/sig_k (q_k = sig_k V_k
+// has unit norm).  If sig_k has biased exponent es, then 1/sig_k <= 2^(1023-es),
+// so no component has a biased exponent above e_B = 2047 - es.  A component
+// v = M 2^(e-1075) (M the 53-bit significand, e its biased exponent) becomes the
+// integer F = sign(v) floor(32 M / 2^(e_B - e)) in units of 2^(e_B - 1080):
+// |F| < 2^58, and the truncation drops less than 2^-55 of the bound.  An
+// element's hop sum adds at most 2L such integers taken from distinct
+// elements, so sum |F| <= sqrt(2L) 2^58 < 2^61 and the integer sum is exact.
+// It is rounded to double once.  FP64 operations per element: the diagonal
+// (2), the hop scale (2), the conversion (2), V_{k-1} (2) and the product with
+// V_k (2), independent of the hop count.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ long long fx_term(double v, int eB, long long neg) {
+    const long long b = __double_as_longlong(v);
+    const int e = int(static_cast<unsigned>(b >> 52) & 0x7FFu);
+    const int r = e == 0 ? 63 : min(max(eB - e, 0), 63);       // zero / subnormal -> 0
+    const unsigned long long m =
+        ((static_cast<unsigned long long>(b) & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull) << 5;
+    const long long f = static_cast<long long>(m >> r);
+    const long long s = (b >> 63) ^ neg;                       // 0 or -1
+    return (f ^ s) - s;
+}
+
+__device__ __forceinline__ long long fx_signed(long long f, long long neg) { return (f ^ neg) - neg; }
+
+__global__ void __launch_bounds__(256, 4) k_cf_apply_hub_fx(HubView h, const double2* __restrict__ Vk,
+                                                            const double2* __restrict__ Vkm1,
+                                                            double2* __restrict__ W, int64_t ld,
+                                                            const int* __restrict__ cols, CFCoef cf, double* part,
+                                                            int L) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    longlong2* row = reinterpret_cast<longlong2*>(sm_raw);          // row u of V_k in fixed point
+    double* lut = reinterpret_cast<double*>(row + h.Ddn);           // 3 (L + 1) diagonal values * sig
+    __shared__ int s_uoff[kMaxHops];
+    __shared__ int s_uneg[kMaxHops];
+    __shared__ double red[32];
+    const int c = cols[blockIdx.y];
+    const int u = blockIdx.x;
+    const int Ddn = int(h.Ddn);
+    const double2* __restrict__ Vc = Vk + int64_t(c) * ld;
+    const double2* __restrict__ Pc = Vkm1 + int64_t(c) * ld;
+    double2* __restrict__ Wc = W + int64_t(c) * ld;
+    const int rbase = u * Ddn;
+    const double sig = cf.sig[c], cB = cf.cB[c];
+    const bool has_prev = (__double_as_longlong(cB) << 1) != 0;
+    const int es = int(static_cast<unsigned long long>(__double_as_longlong(sig)) >> 52) & 0x7FF;
+    const int eB = min(2047 - es, 2100);
+    const uint32_t su = __ldg(h.sup + u);
+    const int nu = __ldg(h.nup + u);
+    for (int d = threadIdx.x; d < Ddn; d += blockDim.x) {
+        const double2 v = Vc[rbase + d];
+        row[d] = make_longlong2(fx_term(v.x, eB, 0), fx_term(v.y, eB, 0));
+    }
+    for (int i = threadIdx.x; i < 3 * (L + 1); i += blockDim.x) {
+        const int p = i % (L + 1), nb = i / (L + 1);
+        lut[i] = sig * (h.U * double(p) - h.Uc * double(nb));
+    }
+    if (threadIdx.x < nu) {
+        const int32_t ent = __ldg(h.hup + int64_t(threadIdx.x) * h.Dup + u);
+        s_uoff[threadIdx.x] = (ent >> 1) * Ddn;
+        s_uneg[threadIdx.x] = -(ent & 1);
+    }
+    __syncthreads();
+    const int core = h.core;
+    const int ubits = core >= 0 ? int((su >> core) & 1u) : 0;
+    // -t sig times the fixed-point unit 2^(eB - 1080) (an exact power of two)
+    const double mts = (-h.t * sig) * __longlong_as_double(static_cast<long long>(eB - 57) << 52);
+    const double mcB = -cB;
+    double dot = 0.0;
+    for (int d = threadIdx.x; d < Ddn; d += blockDim.x) {
+        long long ax = 0, ay = 0;
+        int e = 0;
+        for (; e + 4 <= nu; e += 4) {
+            const double2 v0 = Vc[s_uoff[e] + d], v1 = Vc[s_uoff[e + 1] + d];
+            const double2 v2 = Vc[s_uoff[e + 2] + d], v3 = Vc[s_uoff[e + 3] + d];
+            const long long g0 = s_uneg[e], g1 = s_uneg[e + 1], g2 = s_uneg[e + 2], g3 = s_uneg[e + 3];
+            ax += fx_term(v0.x, eB, g0);
+            ay += fx_term(v0.y, eB, g0);
+            ax += fx_term(v1.x, eB, g1);
+            ay += fx_term(v1.y, eB, g1);
+            ax += fx_term(v2.x, eB, g2);
+            ay += fx_term(v2.y, eB, g2);
+            ax += fx_term(v3.x, eB, g3);
+            ay += fx_term(v3.y, eB, g3);
+        }
+        for (; e < nu; ++e) {
+            const double2 v = Vc[s_uoff[e] + d];
+            const long long g = s_uneg[e];
+            ax += fx_term(v.x, eB, g);
+            ay += fx_term(v.y, eB, g);
+        }
+        const int nd = __ldg(h.ndn + d);
+        e = 0;
+        for (; e + 4 <= nd; e += 4) {
+            const int32_t h0 = __ldg(h.hdn + e * Ddn + d), h1 = __ldg(h.hdn + (e + 1) * Ddn + d);
+            const int32_t h2 = __ldg(h.hdn + (e + 2) * Ddn + d), h3 = __ldg(h.hdn + (e + 3) * Ddn + d);
+            const longlong2 f0 = row[h0 >> 1], f1 = row[h1 >> 1], f2 = row[h2 >> 1], f3 = row[h3 >> 1];
+            const long long g0 = -(h0 & 1), g1 = -(h1 & 1), g2 = -(h2 & 1), g3 = -(h3 & 1);
+            ax += fx_signed(f0.x, g0);
+            ay += fx_signed(f0.y, g0);
+            ax += fx_signed(f1.x, g1);
+            ay += fx_signed(f1.y, g1);
+            ax += fx_signed(f2.x, g2);
+            ay += fx_signed(f2.y, g2);
+            ax += fx_signed(f3.x, g3);
+            ay += fx_signed(f3.y, g3);
+        }
+        for (; e < nd; ++e) {
+            const int32_t hh = __ldg(h.hdn + e * Ddn + d);
+            const longlong2 f = row[hh >> 1];
+            const long long g = -(hh & 1);
+            ax += fx_signed(f.x, g);
+            ay += fx_signed(f.y, g);
+        }
+        const uint32_t sd = __ldg(h.sdn + d);
+        const int nb = core >= 0 ? ubits + int((sd >> core) & 1u) : 0;
+        const double dg = lut[__popc(su & sd) + nb * (L + 1)];
+        const double2 x = Vc[rbase + d];
+        double2 wv;
+        wv.x = fma(mts, __ll2double_rn(ax), dg * x.x);
+        wv.y = fma(mts, __ll2double_rn(ay), dg * x.y);
+        if (has_prev) {
+            const double2 y = __ldcs(Pc + rbase + d);
+            wv.x = fma(mcB, y.x, wv.x);
+            wv.y = fma(mcB, y.y, wv.y);
+        }
+        __stcs(Wc + rbase + d, wv);
+        dot = fma(x.x, wv.x, fma(x.y, wv.y, dot));
+    }
+    double acc[1] = {dot};
+    block_sum<1>(acc, red);
+    if (threadIdx.x == 0) part[int64_t(blockIdx.y) * gridDim.x + blockIdx.x] = acc[0];
+}
+
 // FP32 pass A with two adjacent elements per thread: the up-spin gathers, the
 // V_{k-1} loads and the W stores move 16 bytes (two complex floats) at a time,
 // and the down-spin table is read as 16-bit entries, two per 32-bit load.
@@ -867,6 +1006,9 @@ static void cf_impl(const msb_op* op, const View& view, int64_t n, const void* p
             if (pair)
                 MSB_CUDA(cudaFuncSetAttribute(k_cf_apply_hub_f2x2, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               int(hub_smem)));
+            if (std::is_same<C, double2>::value)
+                MSB_CUDA(cudaFuncSetAttribute(k_cf_apply_hub_fx, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              int(hub_smem)));
         }
     }
     DevBuf<C> Q(3 * size_t(nv) * ld);
@@ -901,7 +1043,12 @@ static void cf_impl(const msb_op* op, const View& view, int64_t n, const void* p
                          nact * (op->hx_flops() + 8.0 * n));
             bool done_hub = false;
             if constexpr (hub) {
-                if (rows && pair) {
+                if (rows && std::is_same<C, double2>::value) {
+                    k_cf_apply_hub_fx<<<dim3(unsigned(nblkA), nact), 256, hub_smem, st>>>(
+                        view, reinterpret_cast<const double2*>(vk), reinterpret_cast<const double2*>(vkm1),
+                        reinterpret_cast<double2*>(wv), ld, cols.p, cf, part.p, L);
+                    done_hub = true;
+                } else if (rows && pair) {
                     k_cf_apply_hub_f2x2<<<dim3(unsigned(nblkA), nact), 256, hub_smem, st>>>(
                         view, reinterpret_cast<const float2*>(vk), reinterpret_cast<const float2*>(vkm1),
                         reinterpret_cast<float2*>(wv), ld, cols.p, cf, part.p, L);
