@@ -19,6 +19,7 @@ problems, no collective on the data path): weak scaling.
 from __future__ import annotations
 
 import argparse
+import math
 import json
 import os
 import statistics
@@ -43,6 +44,8 @@ WORKLOADS = {
 }
 # workloads with one right-hand side per core site (one call, one shared second step)
 SITES = {"hubbard-L12x12rhs-mixed": list(range(12))}
+# clusters of uneven size in one call: name -> (clusters, precision, solve_tol, cf_tol)
+CLUSTERS = {"hubbard-L10-11-12-clusters-mixed": (workloads.BATCH_CLUSTERS, 1, 1e-8, 1e-8)}
 DEFAULT = "hubbard-L12-fp64"
 # random complex-symmetric stress workload: name -> precision, tolerance
 CSR_WORKLOADS = {"random-csr-fp64": (0, 1e-10), "random-csr-mixed": (1, 1e-7)}
@@ -325,7 +328,13 @@ def gpu_arm(args, rank, world):
     native.load()
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
-    wl, prec, stol, ctol = WORKLOADS[args.workload]
+    clusters = None
+    if args.workload in CLUSTERS:
+        clusters, prec, stol, ctol = CLUSTERS[args.workload]
+        wl = clusters[-1]
+        models = [api.model(c.L, c.n_up, c.n_dn, c.t, c.U, c.Uc, core_site=rank % c.L) for c in clusters]
+    else:
+        wl, prec, stol, ctol = WORKLOADS[args.workload]
     core = rank % wl.L
     m = api.model(wl.L, wl.n_up, wl.n_dn, wl.t, wl.U, wl.Uc, core_site=core)
     p = api.map_params(Gamma=wl.Gamma, eta=wl.eta, gs_tol=wl.gs_tol, solve_tol=stol, cf_tol=ctol, precision=prec)
@@ -345,6 +354,9 @@ def gpu_arm(args, rank, world):
     sites = SITES.get(args.workload)
 
     def one_map():
+        if clusters:
+            I, E, info, st = api.rixs_map_clusters(models, p, w_in, w)
+            return I, info, st
         if sites:
             return api.rixs_map_sites(m, p, sites, w_in, w)
         return api.rixs_map_ops(H, Hp, p, w_in, w, out=out)
@@ -385,7 +397,8 @@ def gpu_arm(args, rank, world):
         t = torch.tensor([ms], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-    pts = len(w_in) * len(w) * (len(sites) if sites else 1)
+    n_maps = len(clusters) if clusters else (len(sites) if sites else 1)
+    pts = len(w_in) * len(w) * n_maps
     value = world * pts / (ms * 1e-3)
 
     print(f"[bench] {args.workload}: {ms:.1f} ms per map over {args.steps} steps", file=sys.stderr, flush=True)
@@ -393,8 +406,11 @@ def gpu_arm(args, rank, world):
     torch.cuda.synchronize()
     barrier()
     t0 = time.perf_counter()
-    if args.no_e2e or sites:
-        I_host = out.cpu().numpy()
+    I_host = None
+    if args.no_e2e:
+        pass
+    elif sites or clusters:
+        one_map()          # already the host API: grids in from the host, maps out to the host
     else:
         I_host, info_e2e, _ = api.rixs_map(m, p, w_in, w)
     torch.cuda.synchronize()
@@ -406,7 +422,7 @@ def gpu_arm(args, rank, world):
         e2e_s = float(t.item())
     I_dev = out.cpu().numpy()
     same = (float(np.max(np.abs(I_dev - I_host)) / np.max(np.abs(I_host)))
-            if not sites and np.max(np.abs(I_host)) > 0 else None)
+            if I_host is not None and np.max(np.abs(I_host)) > 0 else None)
 
     peaks = measured_peaks()
     top, roof = dominant_roofline(stats, prec, peaks, args.workload)
@@ -434,10 +450,11 @@ def gpu_arm(args, rank, world):
                    "precision": "FP64" if prec == 0 else "FP32-mixed",
                    "parallelism": f"{world} independent maps (core site = rank)",
                    "l2": "working set (vectors of GBs) larger than L2; no flush needed"},
-        "e2e": {"value": world * pts / e2e_s, "unit": "map points/s",
-                "h2d_bytes_per_step": int(8 * (len(w_in) + len(w))) + 2 * 8 * 4,
-                "d2h_bytes_per_step": int(8 * pts), "seconds": e2e_s,
-                "max_rel_diff_vs_value_map": same},
+        "e2e": None if args.no_e2e else {
+            "value": world * pts / e2e_s, "unit": "map points/s",
+            "h2d_bytes_per_step": int(8 * (len(w_in) + len(w))) + 2 * 8 * 4,
+            "d2h_bytes_per_step": int(8 * pts), "seconds": e2e_s,
+            "max_rel_diff_vs_value_map": same},
         "gpu_launches": launches,
         "roofline": roof,
         "h_apply_alg_gbs": h_gbs,
@@ -449,12 +466,31 @@ def gpu_arm(args, rank, world):
                             "share": round(s["ms"] / total_ms, 4)} for s in stats],
                           key=lambda d: -d["ms"]),
     }
+    if clusters:
+        # the same clusters as separate calls, for comparison (wall clock, one pass)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for mc in models:
+            api.rixs_map(mc, p, w_in, w)
+        torch.cuda.synchronize()
+        line["separate_maps"] = {"seconds": time.perf_counter() - t0,
+                                 "batched_seconds_per_step": ms * 1e-3,
+                                 "what": "the same clusters, one msb_rixs_map call each, one pass"}
+        line["config"]["clusters"] = [
+            {"L": c.L, "n_up": c.n_up, "n_dn": c.n_dn, "dim_ground": math.comb(c.L, c.n_up) * math.comb(c.L, c.n_dn),
+             "dim_intermediate": math.comb(c.L, c.n_up + 1) * math.comb(c.L, c.n_dn)} for c in clusters]
+        line["config"]["parallelism"] = (f"{world} x (one solve on the direct sum of the clusters' H', "
+                                         "one continued fraction over all their columns)")
+        for k in ("L", "n_up", "n_dn", "dim_ground", "dim_intermediate"):
+            line["config"].pop(k)
     return line
 
 
 def reference_arm(args) -> dict:
     """The oracle on the host cores: each step is a bounded sample of the same
     workload (see cpu_baseline_worker), scaled to a whole map."""
+    if args.workload not in WORKLOADS:
+        return {"impl": "reference", "unavailable": f"the oracle sample covers the single-map workloads, not {args.workload}"}
     wl, prec, stol, ctol = WORKLOADS[args.workload]
     vals = []
     for i in range(args.warmup + args.steps):
@@ -479,7 +515,8 @@ def main():
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + sorted(CSR_WORKLOADS), default=DEFAULT)
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + sorted(CSR_WORKLOADS) + sorted(CLUSTERS),
+                    default=DEFAULT)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end map (profiling runs)")
     ap.add_argument("--no-clocks", action="store_true", help="do not sample nvidia-smi (profiling runs)")
@@ -512,7 +549,10 @@ def main():
         return
     line = gpu_arm(args, rank, world)
     if rank == 0:
-        if not args.no_cpu_baseline and world == 1:
+        if not args.no_cpu_baseline and world == 1 and args.workload in CLUSTERS:
+            line["cpu_baseline"] = {"value": None, "unit": "map points/s", "cores": 1, "kind": "oracle",
+                                    "sample": "not sampled for the cluster batch (each cluster is a plain map)"}
+        elif not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = run_cpu_baseline(args.workload)
         elif not args.no_cpu_baseline:
             line["cpu_baseline"] = None

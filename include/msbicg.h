@@ -159,6 +159,20 @@ msb_status msb_op_create_hubbard(const msb_model *model, int intermediate, msb_o
 msb_status msb_op_create_csr(int64_t n, const int64_t *rowptr, const int32_t *col,
                              const double *val, msb_op **out);
 
+/* Direct sum (block-diagonal operator) of n <= 4 Hubbard operators ops[i]
+ * (from msb_op_create_hubbard), each with a real diagonal shift shifts[i]
+ * (HOST array, NULL = all zero): A = (H_0 + s_0) (+) (H_1 + s_1) (+) ...
+ * Vectors of A are the parts' vectors one after another (part 0 first).  One
+ * launch of msb_op_apply or of the solver's MVM covers every part, so one
+ * multi-shift solve (Alg. 1) serves independent clusters of uneven size: with
+ * s_i = -E_G of cluster i, the seed system (A - w_seed - i Gamma) has the
+ * cluster's own E_G in every block and the shifts w_in - w_seed are common.
+ * The parts are NOT owned: they must outlive the sum.  msb_ground_state and
+ * msb_continued_fraction reject a direct sum (MSB_EINVAL).
+ * Errors: MSB_EINVAL (n outside 1..4, a part that is not a Hubbard operator or
+ * lives on another device, a non-finite shift). */
+msb_status msb_op_create_direct_sum(const msb_op *const *ops, const double *shifts, int n, msb_op **out);
+
 msb_status msb_op_dim(const msb_op *op, int64_t *dim);
 
 void msb_op_destroy(msb_op *op);
@@ -302,6 +316,21 @@ int msb_profile_read(msb_kernel_stat *out, int max);
 msb_status msb_rixs_map_sites(const msb_model *model, const msb_map_params *params, const int *sites,
                               int n_sites, const double *w_in, int n_in, const double *w, int n_w,
                               double *I_out, msb_solve_info *info, void *stream);
+
+/* Maps of several independent clusters, models[n_clusters] (n_clusters <= 4;
+ * any L, fillings, boundary and core site each), computed together: one FP64
+ * ground state per cluster, then ONE multi-shift solve on the direct sum of
+ * the clusters' (H'_c - E_G,c) for the concatenated right-hand side
+ * (O2|G_c>)_c (every kernel launch of the solve covers all clusters), then ONE
+ * continued fraction over all n_clusters * n_in columns, each column applying
+ * its own cluster's H (Eqs. 1-2 per cluster).  The solve tolerance is applied
+ * per cluster: the joint residual bound is tol * min_c ||O2 G_c||.
+ * I_out: HOST array n_clusters x n_in x n_w (cluster slowest); E_G_out: HOST
+ * array n_clusters, or NULL.  Requires n_clusters * n_in <= 65535.
+ * Synchronises `stream`.  Errors as msb_rixs_map. */
+msb_status msb_rixs_map_clusters(const msb_model *models, int n_clusters, const msb_map_params *params,
+                                 const double *w_in, int n_in, const double *w, int n_w, double *I_out,
+                                 double *E_G_out, msb_solve_info *info, void *stream);
 
 /* Same map with the operators already built and the result left on the
  * device: H = msb_op_create_hubbard(model, 0), Hp = msb_op_create_hubbard(model,

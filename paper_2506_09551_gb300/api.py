@@ -89,6 +89,23 @@ class Operator:
                                            val.ctypes.data_as(C.POINTER(C.c_double)), C.byref(h)))
         return cls(h)
 
+    @classmethod
+    def direct_sum(cls, ops, shifts=None) -> "Operator":
+        """Block-diagonal (H_0 + s_0) (+) (H_1 + s_1) (+) ... of up to 4 Hubbard operators;
+        keeps the parts alive (the library does not own them)."""
+        arr = (C.c_void_p * len(ops))(*[o.h for o in ops])
+        sh = None
+        if shifts is not None:
+            sh = np.ascontiguousarray(shifts, dtype=np.float64)
+            if len(sh) != len(ops):
+                raise ValueError("one shift per part")
+        h = C.c_void_p()
+        N.check(N.load().msb_op_create_direct_sum(arr, sh.ctypes.data_as(C.POINTER(C.c_double)) if sh is not None
+                                                  else None, len(ops), C.byref(h)))
+        op = cls(h)
+        op._parts = list(ops)
+        return op
+
     def close(self):
         if self.h:
             N.load().msb_op_destroy(self.h)
@@ -198,6 +215,25 @@ def rixs_map_sites(m: N.msb_model, params: N.msb_map_params, sites, w_in, w, all
                                      I.ctypes.data_as(C.POINTER(C.c_double)), C.byref(info), _stream())
     N.check(st, allow=allow_status)
     return I, info.as_dict(), st
+
+
+def rixs_map_clusters(models, params: N.msb_map_params, w_in, w, allow_status=(N.MSB_EMAXITER,)):
+    """Maps of several independent clusters computed together (one solve on their direct
+    sum, one continued fraction over all columns): I[n_clusters, n_in, n_w] (numpy),
+    E_G per cluster (numpy), info dict, status."""
+    arr = (N.msb_model * len(models))(*models)
+    w_in = np.ascontiguousarray(w_in, dtype=np.float64)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    I = np.zeros((len(models), len(w_in), len(w)), dtype=np.float64)
+    E = np.zeros(len(models), dtype=np.float64)
+    info = N.msb_solve_info()
+    st = N.load().msb_rixs_map_clusters(arr, len(models), C.byref(params),
+                                        w_in.ctypes.data_as(C.POINTER(C.c_double)), len(w_in),
+                                        w.ctypes.data_as(C.POINTER(C.c_double)), len(w),
+                                        I.ctypes.data_as(C.POINTER(C.c_double)),
+                                        E.ctypes.data_as(C.POINTER(C.c_double)), C.byref(info), _stream())
+    N.check(st, allow=allow_status)
+    return I, E, info.as_dict(), st
 
 
 def rixs_map(m: N.msb_model, params: N.msb_map_params, w_in, w, G: torch.Tensor | None = None, E_G: float = 0.0,

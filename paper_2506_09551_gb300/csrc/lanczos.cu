@@ -378,6 +378,7 @@ void ground_state(msb_op* H, double tol, int maxit, const double* start, double*
     MSB_REQUIRE(H != nullptr && g != nullptr, "NULL argument");
     MSB_REQUIRE(maxit >= 2, "maxit must be >= 2");
     MSB_REQUIRE(tol > 0, "tol must be > 0");
+    MSB_REQUIRE(H->kind != 2, "a direct sum has no single ground state: take each part's");
     if (H->kind == 0) ground_state_impl(H, H->hub, H->dim, tol, maxit, start, g, out, st);
     else ground_state_impl(H, H->csr, H->dim, tol, maxit, start, g, out, st);
     prof_collect();
@@ -392,9 +393,11 @@ void ground_state(msb_op* H, double tol, int maxit, const double* start, double*
 // ---------------------------------------------------------------------------
 __global__ void k_cf_eval(const double* __restrict__ a, const double* __restrict__ b, int64_t stride_k,
                           const double* __restrict__ n0, const int* __restrict__ cols, const int* __restrict__ depth,
-                          double E0, const double* __restrict__ w, int n_w, double eta, double* I, double* diff) {
+                          const double* __restrict__ E0c, const double* __restrict__ w, int n_w, double eta,
+                          double* I, double* diff) {
     __shared__ double sm[2 * 32];
     const int c = cols[blockIdx.x];
+    const double E0 = E0c[c];
     const int K = depth[c];
     double dmax = 0.0, imax = 0.0;
     for (int i = threadIdx.x; i < n_w; i += blockDim.x) {
@@ -454,20 +457,27 @@ constexpr int kMaxHops = 16;
 // in L2; V_{k-1} and W are streamed with evict-first hints so they do not push
 // it out.  Offsets inside a column are 32-bit (fewer than 2^31 elements for
 // L <= 16).
-template <typename C>
-__global__ void __launch_bounds__(256, 6) k_cf_apply_hub(HubView h, const C* __restrict__ Vk,
+template <typename C, bool Multi>
+__global__ void __launch_bounds__(256, 6) k_cf_apply_hub(HubView h0, const HubView* __restrict__ hv,
+                                                         const int* __restrict__ colq, const C* __restrict__ Vk,
                                                          const C* __restrict__ Vkm1, C* __restrict__ W, int64_t ld,
-                                                         const int* __restrict__ cols, CFCoef cf, double* part,
-                                                         int L) {
+                                                         const int* __restrict__ cols, CFCoef cf, double* part) {
     using S = scalar_t<C>;
+    const int c = cols[blockIdx.y];
+    const int u = blockIdx.x;
+    HubView h = h0;
+    if constexpr (Multi) h = hv[colq[c]];
+    if (Multi && u >= h.Dup) {            // row beyond this column's cluster
+        if (threadIdx.x == 0) part[int64_t(blockIdx.y) * gridDim.x + blockIdx.x] = 0.0;
+        return;
+    }
+    const int L = h.L;
     extern __shared__ __align__(16) unsigned char sm_raw[];
     C* row = reinterpret_cast<C*>(sm_raw);                          // Ddn values of row u
     S* lut = reinterpret_cast<S*>(row + h.Ddn);                     // 3 (L + 1) diagonal values * sig
     __shared__ int s_uoff[kMaxHops];
     __shared__ S s_usg[kMaxHops];
     __shared__ double red[32];
-    const int c = cols[blockIdx.y];
-    const int u = blockIdx.x;
     const int Ddn = int(h.Ddn);
     const C* __restrict__ Vc = Vk + int64_t(c) * ld;
     const C* __restrict__ Pc = Vkm1 + int64_t(c) * ld;
@@ -596,19 +606,28 @@ __device__ __forceinline__ long long fx_term(double v, int eB, long long neg) {
 
 __device__ __forceinline__ long long fx_signed(long long f, long long neg) { return (f ^ neg) - neg; }
 
-__global__ void __launch_bounds__(256, 4) k_cf_apply_hub_fx(HubView h, const double2* __restrict__ Vk,
+template <bool Multi>
+__global__ void __launch_bounds__(256, 4) k_cf_apply_hub_fx(HubView h0, const HubView* __restrict__ hv,
+                                                            const int* __restrict__ colq,
+                                                            const double2* __restrict__ Vk,
                                                             const double2* __restrict__ Vkm1,
                                                             double2* __restrict__ W, int64_t ld,
-                                                            const int* __restrict__ cols, CFCoef cf, double* part,
-                                                            int L) {
+                                                            const int* __restrict__ cols, CFCoef cf, double* part) {
+    const int c = cols[blockIdx.y];
+    const int u = blockIdx.x;
+    HubView h = h0;
+    if constexpr (Multi) h = hv[colq[c]];
+    if (Multi && u >= h.Dup) {            // row beyond this column's cluster
+        if (threadIdx.x == 0) part[int64_t(blockIdx.y) * gridDim.x + blockIdx.x] = 0.0;
+        return;
+    }
+    const int L = h.L;
     extern __shared__ __align__(16) unsigned char sm_raw[];
     longlong2* row = reinterpret_cast<longlong2*>(sm_raw);          // row u of V_k in fixed point
     double* lut = reinterpret_cast<double*>(row + h.Ddn);           // 3 (L + 1) diagonal values * sig
     __shared__ int s_uoff[kMaxHops];
     __shared__ int s_uneg[kMaxHops];
     __shared__ double red[32];
-    const int c = cols[blockIdx.y];
-    const int u = blockIdx.x;
     const int Ddn = int(h.Ddn);
     const double2* __restrict__ Vc = Vk + int64_t(c) * ld;
     const double2* __restrict__ Pc = Vkm1 + int64_t(c) * ld;
@@ -709,18 +728,28 @@ __global__ void __launch_bounds__(256, 4) k_cf_apply_hub_fx(HubView h, const dou
 // V_{k-1} loads and the W stores move 16 bytes (two complex floats) at a time,
 // and the down-spin table is read as 16-bit entries, two per 32-bit load.
 // Needs an even Ddn (rows start on 16-byte boundaries) and Ddn < 32768.
-__global__ void __launch_bounds__(256, 6) k_cf_apply_hub_f2x2(HubView h, const float2* __restrict__ Vk,
+template <bool Multi>
+__global__ void __launch_bounds__(256, 6) k_cf_apply_hub_f2x2(HubView h0, const HubView* __restrict__ hv,
+                                                              const int* __restrict__ colq,
+                                                              const float2* __restrict__ Vk,
                                                               const float2* __restrict__ Vkm1, float2* __restrict__ W,
                                                               int64_t ld, const int* __restrict__ cols, CFCoef cf,
-                                                              double* part, int L) {
+                                                              double* part) {
+    const int c = cols[blockIdx.y];
+    const int u = blockIdx.x;
+    HubView h = h0;
+    if constexpr (Multi) h = hv[colq[c]];
+    if (Multi && u >= h.Dup) {            // row beyond this column's cluster
+        if (threadIdx.x == 0) part[int64_t(blockIdx.y) * gridDim.x + blockIdx.x] = 0.0;
+        return;
+    }
+    const int L = h.L;
     extern __shared__ __align__(16) unsigned char sm_raw[];
     float2* row = reinterpret_cast<float2*>(sm_raw);                // Ddn values of row u
     float* lut = reinterpret_cast<float*>(row + h.Ddn);             // 3 (L + 1) diagonal values * sig
     __shared__ int s_uoff[kMaxHops];
     __shared__ float s_usg[kMaxHops];
     __shared__ double red[32];
-    const int c = cols[blockIdx.y];
-    const int u = blockIdx.x;
     const int Ddn = int(h.Ddn);
     const int half = Ddn >> 1;
     const float2* __restrict__ Vc = Vk + int64_t(c) * ld;
@@ -889,7 +918,8 @@ __device__ __forceinline__ void orth_step(float4 v, float4& x, float m, double&,
 
 template <typename C>
 __global__ void __launch_bounds__(256) k_cf_orth(const C* __restrict__ Vk, C* __restrict__ W, int64_t ld,
-                                                 const int* __restrict__ cols, CFCoef cf, double* part) {
+                                                 const int* __restrict__ cols, const int64_t* __restrict__ clen,
+                                                 CFCoef cf, double* part) {
     using S = scalar_t<C>;
     using V16 = typename std::conditional<std::is_same<S, float>::value, float4, double2>::type;
     constexpr int per = sizeof(V16) / sizeof(C);     // complex elements per 16-byte load
@@ -897,7 +927,7 @@ __global__ void __launch_bounds__(256) k_cf_orth(const C* __restrict__ Vk, C* __
     const int c = cols[blockIdx.y];
     const V16* __restrict__ v4 = reinterpret_cast<const V16*>(Vk + int64_t(c) * ld);
     V16* __restrict__ w4 = reinterpret_cast<V16*>(W + int64_t(c) * ld);
-    const int64_t nv = ld / per;
+    const int64_t nv = clen[c] / per;                 // column length, rounded up to even
     const S mc = S(-cf.cC[c]);
     double acc = 0.0;
     float hi = 0.f, lo = 0.f;
@@ -937,18 +967,21 @@ __global__ void k_cf_reduce_b(const double* part, int nblk, const int* cols, dou
 }
 
 // V_0 = phi (copied: the input is not modified; padding zeroed); the other two
-// vector blocks get a zero padding; partial ||phi||^2.
+// vector blocks get a zero padding; partial ||phi||^2.  Column c of phi starts
+// at c * ldphi and has nlen[c] elements.
 template <typename C>
-__global__ void __launch_bounds__(256) k_cf_start(const C* __restrict__ phi, C* __restrict__ V0, C* __restrict__ V1,
-                                                  C* __restrict__ V2, int64_t n, int64_t ld, double* part) {
+__global__ void __launch_bounds__(256) k_cf_start(const C* __restrict__ phi, int64_t ldphi,
+                                                  const int64_t* __restrict__ nlen, C* __restrict__ V0,
+                                                  C* __restrict__ V1, C* __restrict__ V2, int64_t ld, double* part) {
     using S = scalar_t<C>;
     __shared__ double sm[32];
     const int c = blockIdx.y;
+    const int64_t n = nlen[c];
     double acc = 0.0;
     float hi = 0.f, lo = 0.f;
     for (int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < ld; s += int64_t(gridDim.x) * blockDim.x) {
         C x = mk(S(0), S(0));
-        if (s < n) x = phi[int64_t(c) * n + s];
+        if (s < n) x = phi[int64_t(c) * ldphi + s];
         V0[int64_t(c) * ld + s] = x;
         if (s >= n) {
             V1[int64_t(c) * ld + s] = x;
@@ -981,50 +1014,77 @@ __global__ void k_cf_setup(const double* part, int nblk, double* n0, CFCoef cf) 
 }
 
 template <class View, typename C>
-static void cf_impl(const msb_op* op, const View& view, int64_t n, const void* phi_v, int nv, double E0, const double* w,
-                    int n_w, double eta, double cf_tol, int check, int maxdepth, double* I_out, CFResult& out,
-                    cudaStream_t st, bool I_dev) {
+static void cf_impl(const CFColumns& P, const View& view, const double* w, int n_w, double eta, double cf_tol,
+                    int check, int maxdepth, double* I_out, CFResult& out, cudaStream_t st, bool I_dev) {
     constexpr bool hub = std::is_same<View, HubView>::value;
-    const int64_t ld = (n + 1) / 2 * 2;
-    const double vb = double(sizeof(C)) * double(n);        // one complex vector
-    const C* phi = (const C*)phi_v;
+    const int nv = P.nv;
+    const bool multi = P.ops.size() > 1;
+    std::vector<int64_t> nlen(nv), clen(nv);
+    int64_t ld = 0;
+    for (int c = 0; c < nv; ++c) {
+        nlen[c] = P.ops[P.q[c]]->dim;
+        clen[c] = (nlen[c] + 1) / 2 * 2;     // 16-byte loads in the orth pass; the padding stays zero
+        ld = std::max(ld, clen[c]);
+    }
+    const C* phi = (const C*)P.phi;
     const int per = int(16 / sizeof(C));
     const int grid = grid_for(ld / per, 256, 4);
     int64_t hub_smem = 0;
-    int L = 0;
     bool rows = false, pair = false;
     int nblkA = grid;
+    std::vector<HubView> hviews;
     if constexpr (hub) {
-        L = op->model.L;
-        hub_smem = view.Ddn * int64_t(sizeof(C)) + 3 * (L + 1) * 8;
-        rows = hub_smem <= 160 * 1024 && view.Wup <= kMaxHops && view.Dup * view.Ddn < (int64_t(1) << 31);
+        int64_t maxDdn = 0, maxDup = 0;
+        int maxL = 0;
+        rows = true;
+        pair = std::is_same<C, float2>::value;
+        for (const msb_op* o : P.ops) {
+            const HubView& h = o->hub;
+            hviews.push_back(h);
+            maxDdn = std::max(maxDdn, h.Ddn);
+            maxDup = std::max(maxDup, h.Dup);
+            maxL = std::max(maxL, h.L);
+            rows = rows && h.Wup <= kMaxHops && h.Dup * h.Ddn < (int64_t(1) << 31);
+            pair = pair && h.Ddn % 2 == 0 && h.hdn16 != nullptr;
+        }
+        hub_smem = maxDdn * int64_t(sizeof(C)) + 3 * (maxL + 1) * 8;
+        rows = rows && hub_smem <= 160 * 1024;
         if (rows) {
-            nblkA = int(view.Dup);
-            MSB_CUDA(cudaFuncSetAttribute(k_cf_apply_hub<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          int(hub_smem)));
-            pair = std::is_same<C, float2>::value && view.Ddn % 2 == 0 && view.hdn16 != nullptr;
-            if (pair)
-                MSB_CUDA(cudaFuncSetAttribute(k_cf_apply_hub_f2x2, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              int(hub_smem)));
+            nblkA = int(maxDup);
+            const void* fn = nullptr;
             if (std::is_same<C, double2>::value)
-                MSB_CUDA(cudaFuncSetAttribute(k_cf_apply_hub_fx, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              int(hub_smem)));
+                fn = multi ? (const void*)k_cf_apply_hub_fx<true> : (const void*)k_cf_apply_hub_fx<false>;
+            else if (pair)
+                fn = multi ? (const void*)k_cf_apply_hub_f2x2<true> : (const void*)k_cf_apply_hub_f2x2<false>;
+            else
+                fn = multi ? (const void*)k_cf_apply_hub<C, true> : (const void*)k_cf_apply_hub<C, false>;
+            MSB_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(hub_smem)));
         }
     }
+    MSB_REQUIRE(!multi || rows, "a batch of clusters needs the row-tiled Hubbard apply (L <= 16, <= 16 hops)");
     DevBuf<C> Q(3 * size_t(nv) * ld);
     DevBuf<double> part(size_t(std::max(grid, nblkA)) * nv), a(size_t(maxdepth) * nv), b(size_t(maxdepth) * nv),
-        n0(nv), sig(nv), cB(nv), cC(nv), I(size_t(nv) * n_w), diff(2 * size_t(nv)), wdev(n_w);
-    DevBuf<int> cols(nv), depth(nv);
+        n0(nv), sig(nv), cB(nv), cC(nv), I(size_t(nv) * n_w), diff(2 * size_t(nv)), wdev(n_w), E0d(nv);
+    DevBuf<int> cols(nv), depth(nv), colq(nv);
+    DevBuf<int64_t> nlen_d(nv), clen_d(nv);
+    DevBuf<HubView> hv(std::max<size_t>(1, hviews.size()));
+    if (!hviews.empty()) hv.upload(hviews.data(), hviews.size(), st);
     CFCoef cf{sig.p, cB.p, cC.p};
     wdev.upload(w, n_w, st);
+    E0d.upload(P.E0.data(), nv, st);
+    colq.upload(P.q.data(), nv, st);
+    nlen_d.upload(nlen.data(), nv, st);
+    clen_d.upload(clen.data(), nv, st);
     std::vector<int> hcols(nv), hdepth(nv, 0);
     MSB_CUDA(cudaMemsetAsync(I.p, 0, I.bytes(), st));
     C* vk = Q.p;
     C* vkm1 = Q.p + size_t(nv) * ld;
     C* wv = Q.p + 2 * size_t(nv) * ld;
+    double all_elems = 0;
+    for (int c = 0; c < nv; ++c) all_elems += double(nlen[c]);
     {
-        ProfScope ps("cf_start", st, nv * 2 * vb, nv * 4.0 * n);
-        k_cf_start<C><<<dim3(grid, nv), 256, 0, st>>>(phi, vk, vkm1, wv, n, ld, part.p);
+        ProfScope ps("cf_start", st, 2.0 * all_elems * sizeof(C), 4.0 * all_elems);
+        k_cf_start<C><<<dim3(grid, nv), 256, 0, st>>>(phi, P.ldphi, nlen_d.p, vk, vkm1, wv, ld, part.p);
     }
     { ProfScope ps("cf_reduce", st, 0, 0); k_cf_setup<<<nv, 256, 0, st>>>(part.p, grid, n0.p, cf); }
     out.launches += 2;
@@ -1036,40 +1096,70 @@ static void cf_impl(const msb_op* op, const View& view, int64_t n, const void* p
     for (int c = 0; c < nv; ++c)
         if (hn0[c] > 0.0) hcols[nact++] = c;
     cols.upload(hcols.data(), std::max(nact, 1), st);
+    // algorithmic bytes / flops of the active columns (recounted when the set shrinks)
+    double act_elems = 0, apply_bytes = 0, apply_flops = 0;
+    auto recount = [&] {
+        act_elems = apply_bytes = apply_flops = 0;
+        for (int i = 0; i < nact; ++i) {
+            const int c = hcols[i];
+            const msb_op* o = P.ops[P.q[c]];
+            act_elems += double(nlen[c]);
+            apply_bytes += 3.0 * double(nlen[c]) * sizeof(C) + o->matrix_bytes(sizeof(C));
+            apply_flops += o->hx_flops() + 8.0 * double(nlen[c]);
+        }
+    };
+    recount();
+    const dim3 gridA(unsigned(nblkA), 1);
     int k = 0;
     while (nact > 0 && k < maxdepth) {
         {
-            ProfScope ps("cf_apply", st, nact * (3 * vb + op->matrix_bytes(sizeof(C))),
-                         nact * (op->hx_flops() + 8.0 * n));
+            ProfScope ps("cf_apply", st, apply_bytes, apply_flops);
             bool done_hub = false;
             if constexpr (hub) {
+                const dim3 g(gridA.x, unsigned(nact));
                 if (rows && std::is_same<C, double2>::value) {
-                    k_cf_apply_hub_fx<<<dim3(unsigned(nblkA), nact), 256, hub_smem, st>>>(
-                        view, reinterpret_cast<const double2*>(vk), reinterpret_cast<const double2*>(vkm1),
-                        reinterpret_cast<double2*>(wv), ld, cols.p, cf, part.p, L);
+                    auto x = reinterpret_cast<const double2*>(vk);
+                    auto xm = reinterpret_cast<const double2*>(vkm1);
+                    auto y = reinterpret_cast<double2*>(wv);
+                    if (multi)
+                        k_cf_apply_hub_fx<true><<<g, 256, hub_smem, st>>>(view, hv.p, colq.p, x, xm, y, ld, cols.p,
+                                                                          cf, part.p);
+                    else
+                        k_cf_apply_hub_fx<false><<<g, 256, hub_smem, st>>>(view, hv.p, colq.p, x, xm, y, ld,
+                                                                           cols.p, cf, part.p);
                     done_hub = true;
                 } else if (rows && pair) {
-                    k_cf_apply_hub_f2x2<<<dim3(unsigned(nblkA), nact), 256, hub_smem, st>>>(
-                        view, reinterpret_cast<const float2*>(vk), reinterpret_cast<const float2*>(vkm1),
-                        reinterpret_cast<float2*>(wv), ld, cols.p, cf, part.p, L);
+                    auto x = reinterpret_cast<const float2*>(vk);
+                    auto xm = reinterpret_cast<const float2*>(vkm1);
+                    auto y = reinterpret_cast<float2*>(wv);
+                    if (multi)
+                        k_cf_apply_hub_f2x2<true><<<g, 256, hub_smem, st>>>(view, hv.p, colq.p, x, xm, y, ld,
+                                                                            cols.p, cf, part.p);
+                    else
+                        k_cf_apply_hub_f2x2<false><<<g, 256, hub_smem, st>>>(view, hv.p, colq.p, x, xm, y, ld,
+                                                                             cols.p, cf, part.p);
                     done_hub = true;
                 } else if (rows) {
-                    k_cf_apply_hub<C><<<dim3(unsigned(nblkA), nact), 256, hub_smem, st>>>(view, vk, vkm1, wv, ld,
-                                                                                          cols.p, cf, part.p, L);
+                    if (multi)
+                        k_cf_apply_hub<C, true><<<g, 256, hub_smem, st>>>(view, hv.p, colq.p, vk, vkm1, wv, ld,
+                                                                          cols.p, cf, part.p);
+                    else
+                        k_cf_apply_hub<C, false><<<g, 256, hub_smem, st>>>(view, hv.p, colq.p, vk, vkm1, wv, ld,
+                                                                           cols.p, cf, part.p);
                     done_hub = true;
                 }
             }
             if (!done_hub)
-                k_cf_apply_gen<View, C><<<dim3(grid, nact), 256, 0, st>>>(view, vk, vkm1, wv, n, ld, cols.p, cf,
-                                                                          part.p);
+                k_cf_apply_gen<View, C><<<dim3(grid, nact), 256, 0, st>>>(view, vk, vkm1, wv, nlen[0], ld, cols.p,
+                                                                          cf, part.p);
         }
         {
             ProfScope ps("cf_reduce", st, 0, 0);
             k_cf_reduce_a<<<nact, 256, 0, st>>>(part.p, rows ? nblkA : grid, cols.p, a.p, nv, k, cf);
         }
         {
-            ProfScope ps("cf_orth", st, nact * 3 * vb, nact * 8.0 * n);
-            k_cf_orth<C><<<dim3(grid, nact), 256, 0, st>>>(vk, wv, ld, cols.p, cf, part.p);
+            ProfScope ps("cf_orth", st, 3.0 * act_elems * sizeof(C), 8.0 * act_elems);
+            k_cf_orth<C><<<dim3(grid, nact), 256, 0, st>>>(vk, wv, ld, cols.p, clen_d.p, cf, part.p);
         }
         {
             ProfScope ps("cf_reduce", st, 0, 0);
@@ -1089,7 +1179,7 @@ static void cf_impl(const msb_op* op, const View& view, int64_t n, const void* p
             depth.upload(hdepth.data(), nv, st);
             {
                 ProfScope ps("cf_eval", st, 0, 20.0 * nact * n_w * double(k));
-                k_cf_eval<<<nact, 128, 0, st>>>(a.p, b.p, nv, n0.p, cols.p, depth.p, E0, wdev.p, n_w, eta, I.p,
+                k_cf_eval<<<nact, 128, 0, st>>>(a.p, b.p, nv, n0.p, cols.p, depth.p, E0d.p, wdev.p, n_w, eta, I.p,
                                                 diff.p);
             }
             ++out.launches;
@@ -1102,7 +1192,10 @@ static void cf_impl(const msb_op* op, const View& view, int64_t n, const void* p
                 if (k > check && hdiff[2 * c] <= cf_tol * hdiff[2 * c + 1]) fin = true;
                 if (!fin) hcols[keep++] = c;
             }
-            nact = keep;
+            if (keep != nact) {
+                nact = keep;
+                recount();
+            }
             cols.upload(hcols.data(), std::max(nact, 1), st);
         }
     }
@@ -1112,21 +1205,50 @@ static void cf_impl(const msb_op* op, const View& view, int64_t n, const void* p
     out.depth = hdepth;
 }
 
-void continued_fraction(msb_op* H, const void* phi, int n_vec, double E0, const double* w, int n_w, double eta,
-                        double cf_tol, int cf_check, int cf_maxdepth, msb_precision prec, double* I_out,
-                        CFResult& out, cudaStream_t st, bool I_dev) {
-    MSB_REQUIRE(H != nullptr && phi != nullptr && w != nullptr && I_out != nullptr, "NULL argument");
+static void cf_check_args(int n_vec, const double* w, int n_w, double eta, int cf_check, int cf_maxdepth,
+                          double* I_out) {
+    MSB_REQUIRE(w != nullptr && I_out != nullptr, "NULL argument");
     MSB_REQUIRE(n_vec >= 1 && n_vec <= 65535, "n_vec must be in 1..65535");
     MSB_REQUIRE(n_w >= 1, "n_w must be >= 1");
     MSB_REQUIRE(eta > 0, "eta must be > 0");
     MSB_REQUIRE(cf_check >= 1 && cf_maxdepth >= cf_check, "need 1 <= cf_check <= cf_maxdepth");
+}
+
+void continued_fraction(msb_op* H, const void* phi, int n_vec, double E0, const double* w, int n_w, double eta,
+                        double cf_tol, int cf_check, int cf_maxdepth, msb_precision prec, double* I_out,
+                        CFResult& out, cudaStream_t st, bool I_dev) {
+    MSB_REQUIRE(H != nullptr && phi != nullptr, "NULL argument");
+    cf_check_args(n_vec, w, n_w, eta, cf_check, cf_maxdepth, I_out);
+    MSB_REQUIRE(H->kind != 2, "the continued fraction of a direct sum mixes its parts: use one part per column");
+    CFColumns P;
+    P.phi = phi;
+    P.ldphi = H->dim;
+    P.nv = n_vec;
+    P.ops = {H};
+    P.q.assign(n_vec, 0);
+    P.E0.assign(n_vec, E0);
     if (prec == MSB_FP64) {
-        if (H->kind == 0) cf_impl<HubView, double2>(H, H->hub, H->dim, phi, n_vec, E0, w, n_w, eta, cf_tol, cf_check, cf_maxdepth, I_out, out, st, I_dev);
-        else cf_impl<CsrView, double2>(H, H->csr, H->dim, phi, n_vec, E0, w, n_w, eta, cf_tol, cf_check, cf_maxdepth, I_out, out, st, I_dev);
+        if (H->kind == 0) cf_impl<HubView, double2>(P, H->hub, w, n_w, eta, cf_tol, cf_check, cf_maxdepth, I_out, out, st, I_dev);
+        else cf_impl<CsrView, double2>(P, H->csr, w, n_w, eta, cf_tol, cf_check, cf_maxdepth, I_out, out, st, I_dev);
     } else {
-        if (H->kind == 0) cf_impl<HubView, float2>(H, H->hub, H->dim, phi, n_vec, E0, w, n_w, eta, cf_tol, cf_check, cf_maxdepth, I_out, out, st, I_dev);
-        else cf_impl<CsrView, float2>(H, H->csr, H->dim, phi, n_vec, E0, w, n_w, eta, cf_tol, cf_check, cf_maxdepth, I_out, out, st, I_dev);
+        if (H->kind == 0) cf_impl<HubView, float2>(P, H->hub, w, n_w, eta, cf_tol, cf_check, cf_maxdepth, I_out, out, st, I_dev);
+        else cf_impl<CsrView, float2>(P, H->csr, w, n_w, eta, cf_tol, cf_check, cf_maxdepth, I_out, out, st, I_dev);
     }
+    prof_collect();
+}
+
+void continued_fraction_columns(const CFColumns& P, const double* w, int n_w, double eta, double cf_tol,
+                                int cf_check, int cf_maxdepth, msb_precision prec, double* I_out, CFResult& out,
+                                cudaStream_t st) {
+    MSB_REQUIRE(P.phi != nullptr && !P.ops.empty() && int(P.q.size()) == P.nv && int(P.E0.size()) == P.nv,
+                "inconsistent column description");
+    cf_check_args(P.nv, w, n_w, eta, cf_check, cf_maxdepth, I_out);
+    for (const msb_op* o : P.ops) MSB_REQUIRE(o != nullptr && o->kind == 0, "cluster columns need Hubbard operators");
+    for (int c = 0; c < P.nv; ++c) MSB_REQUIRE(P.q[c] >= 0 && P.q[c] < int(P.ops.size()), "column cluster out of range");
+    if (prec == MSB_FP64)
+        cf_impl<HubView, double2>(P, P.ops[0]->hub, w, n_w, eta, cf_tol, cf_check, cf_maxdepth, I_out, out, st, false);
+    else
+        cf_impl<HubView, float2>(P, P.ops[0]->hub, w, n_w, eta, cf_tol, cf_check, cf_maxdepth, I_out, out, st, false);
     prof_collect();
 }
 
@@ -1321,6 +1443,7 @@ extern "C" msb_status msb_ground_state_noalloc(msb_op* H, double tol, int maxit,
         int dev = 0;
         MSB_CUDA(cudaGetDevice(&dev));
         MSB_REQUIRE(dev == H->device, "the operator was created on another device");
+        MSB_REQUIRE(H->kind != 2, "a direct sum has no single ground state: take each part's");
         cudaStream_t st = (cudaStream_t)stream;
         msb::GroundResult r;
         if (H->kind == 0) msb::ground_state_noalloc_impl(H->hub, H->dim, tol, maxit, start, g, r, st);

@@ -498,15 +498,13 @@ struct SolverImpl {
         }
     }
 
-    void one_block_direct(const void* viewp, bool hub) {
+    template <class View>
+    void one_block_direct(const View& view) {
         {
             ProfScope ps("shift_scalars", st, 0, 0);
             k_block_begin<<<1, kScalarThreads, 0, st>>>(state.p, sh, pr.ns);
         }
-        for (int i = 0; i < B; ++i) {
-            if (hub) iteration(*(const HubView*)viewp);
-            else iteration(*(const CsrView*)viewp);
-        }
+        for (int i = 0; i < B; ++i) iteration(view);
         flush();
     }
 
@@ -551,10 +549,9 @@ struct SolverImpl {
         if (prof_on()) {
             // Profiled: direct launches, one sync per block to attribute the
             // fused update's work (shifts and iterations it carried).
-            constexpr bool hub = std::is_same<View, HubView>::value;
             SeedState hs;
             for (;;) {
-                one_block_direct(&view, hub);
+                one_block_direct(view);
                 launches += per_block;
                 ++blocks;
                 MSB_CUDA(cudaMemcpyAsync(&hs, state.p, sizeof(SeedState), cudaMemcpyDeviceToHost, st));
@@ -641,10 +638,14 @@ void multishift_solve(msb_op* op, const SolveProblem& pr, SolveResult& out, cuda
     MSB_REQUIRE(pr.ns >= 1 && pr.ns <= kMaxShifts, "n_shifts must be in 1..4096");
     if (pr.prec == MSB_FP64) {
         SolverImpl<double2> s(pr, st);
-        if (op->kind == 0) s.run(op, op->hub, out); else s.run(op, op->csr, out);
+        if (op->kind == 0) s.run(op, op->hub, out);
+        else if (op->kind == 1) s.run(op, op->csr, out);
+        else s.run(op, op->sum, out);
     } else {
         SolverImpl<float2> s(pr, st);
-        if (op->kind == 0) s.run(op, op->hub, out); else s.run(op, op->csr, out);
+        if (op->kind == 0) s.run(op, op->hub, out);
+        else if (op->kind == 1) s.run(op, op->csr, out);
+        else s.run(op, op->sum, out);
     }
 }
 

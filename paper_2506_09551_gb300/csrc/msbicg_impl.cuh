@@ -76,6 +76,24 @@ void continued_fraction(msb_op* H, const void* phi, int n_vec, double E0, const 
                         double eta, double cf_tol, int cf_check, int cf_maxdepth, msb_precision prec,
                         double* I_out, CFResult& out, cudaStream_t st, bool I_on_device = false);
 
+// Columns of one continued-fraction run.  Column c starts at phi + c * ldphi
+// (elements), has ops[q[c]]->dim elements and applies ops[q[c]] with the energy
+// origin E0[c]: one operator for all columns, or, for a batch of clusters, each
+// column its own cluster's Hubbard H (one launch per step covers all columns).
+struct CFColumns {
+    const void* phi = nullptr;
+    int64_t ldphi = 0;
+    int nv = 0;
+    std::vector<const msb_op*> ops;
+    std::vector<int> q;
+    std::vector<double> E0;
+};
+
+// The batch form: Hubbard operators only; I_out on the host (nv x n_w).
+void continued_fraction_columns(const CFColumns& P, const double* w, int n_w, double eta, double cf_tol,
+                                int cf_check, int cf_maxdepth, msb_precision prec, double* I_out, CFResult& out,
+                                cudaStream_t st);
+
 // Work runs on an internal non-blocking stream ordered after the caller's
 // stream; finish() orders the caller's stream after it and synchronises.
 struct StreamScope {

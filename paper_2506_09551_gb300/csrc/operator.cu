@@ -1,4 +1,5 @@
 // Operator objects and the plain apply y = (A + c0) x (the MVM of Alg. 1).
+#include <cmath>
 #include <memory>
 
 #include "operator.cuh"
@@ -47,6 +48,7 @@ static void build_hubbard(msb_op* op, const msb_model& m, int intermediate) {
     h.sup = op->sup.p; h.sdn = op->sdn.p;
     h.t = m.t; h.U = m.U; h.Uc = m.Uc;
     h.core = intermediate ? m.core_site : -1;
+    h.L = m.L;
     op->dim = h.Dup * h.Ddn;
     double nh = 0;
     for (uint8_t c : cu) nh += double(c) * double(h.Ddn);
@@ -74,6 +76,28 @@ static void build_csr(msb_op* op, int64_t n, const int64_t* rowptr, const int32_
     MSB_CUDA(cudaDeviceSynchronize());
     op->csr = CsrView{n, op->rowptr.p, op->col.p, op->val64.p, op->val32.p};
     op->offdiag = double(nnz);
+}
+
+static void build_sum(msb_op* op, const msb_op* const* ops, const double* shifts, int n) {
+    MSB_REQUIRE(ops != nullptr && n >= 1 && n <= kMaxParts, "need 1..4 operators");
+    op->kind = 2;
+    SumView& v = op->sum;
+    v.np = n;
+    int64_t off = 0;
+    MSB_CUDA(cudaGetDevice(&op->device));
+    for (int i = 0; i < n; ++i) {
+        MSB_REQUIRE(ops[i] != nullptr && ops[i]->kind == 0, "every part must be a Hubbard operator");
+        MSB_REQUIRE(ops[i]->device == op->device, "every part must live on the current device");
+        v.part[i] = ops[i]->hub;
+        v.off[i] = off;
+        v.shift[i] = shifts ? shifts[i] : 0.0;
+        MSB_REQUIRE(std::isfinite(v.shift[i]), "shifts must be finite");
+        off += ops[i]->dim;
+        op->offdiag += ops[i]->offdiag;
+        op->parts.push_back(ops[i]);
+    }
+    for (int i = n; i <= kMaxParts; ++i) v.off[i] = off;
+    op->dim = off;
 }
 
 // ---------------------------------------------------------------------------
@@ -113,7 +137,8 @@ void op_apply(msb_op* op, double2 c0, const void* x, void* y, int nvec, msb_prec
     MSB_REQUIRE(nvec >= 1 && nvec <= 65535, "nvec must be in 1..65535");
     MSB_REQUIRE(prec == MSB_FP64 || prec == MSB_FP32_MIXED, "unknown precision");
     if (op->kind == 0) launch_apply(op, op->hub, op->dim, c0, x, y, nvec, prec, st);
-    else launch_apply(op, op->csr, op->dim, c0, x, y, nvec, prec, st);
+    else if (op->kind == 1) launch_apply(op, op->csr, op->dim, c0, x, y, nvec, prec, st);
+    else launch_apply(op, op->sum, op->dim, c0, x, y, nvec, prec, st);
     prof_collect();
 }
 
@@ -139,6 +164,17 @@ extern "C" msb_status msb_op_create_csr(int64_t n, const int64_t* rowptr, const 
         msb::require_device();
         auto op = std::make_unique<msb_op>();
         msb::build_csr(op.get(), n, rowptr, col, val);
+        *out = op.release();
+    });
+}
+
+extern "C" msb_status msb_op_create_direct_sum(const msb_op* const* ops, const double* shifts, int n,
+                                               msb_op** out) {
+    return msb::guard("msb_op_create_direct_sum", [&] {
+        MSB_REQUIRE(out != nullptr, "out is NULL");
+        msb::require_device();
+        auto op = std::make_unique<msb_op>();
+        msb::build_sum(op.get(), ops, shifts, n);
         *out = op.release();
     });
 }

@@ -68,6 +68,7 @@ struct HubView {
     const uint32_t* sdn;
     double t, U, Uc;
     int core;              // core-hole site, -1: none (plain H)
+    int L;                 // sites
 
     // U popc(u & d) - Uc (n_{j,up} + n_{j,dn}), in the vector's precision (no
     // FP64 work in the FP32 path).
@@ -108,6 +109,41 @@ struct HubView {
 };
 
 // ----------------------------------------------------------------------------
+// Direct sum of Hubbard operators (block diagonal): element s in
+// [off[i], off[i+1]) belongs to part i, and (A x)[s] = (H_i x_i)[s - off[i]]
+// + shift[i] x[s].  One launch over the concatenated vector applies every part,
+// so one Krylov recurrence serves independent clusters of uneven size.
+// ----------------------------------------------------------------------------
+constexpr int kMaxParts = 4;
+
+struct SumView {
+    int np;
+    int64_t off[kMaxParts + 1];
+    double shift[kMaxParts];
+    HubView part[kMaxParts];
+
+    template <int I, typename V>
+    __device__ __forceinline__ V hx_part(int64_t s, const V* __restrict__ x, V xs) const {
+        using S = scalar_t<V>;
+        const V h = part[I].hx(s - off[I], x + off[I], xs);
+        return vaxpy(S(shift[I]), xs, h);
+    }
+
+    template <typename V>
+    __device__ __forceinline__ V hx(int64_t s, const V* __restrict__ x, V xs) const {
+        // part index by comparison (no dynamic indexing of the parameter arrays)
+        if (np > 1 && s >= off[1]) {
+            if (np > 2 && s >= off[2]) {
+                if (np > 3 && s >= off[3]) return hx_part<3>(s, x, xs);
+                return hx_part<2>(s, x, xs);
+            }
+            return hx_part<1>(s, x, xs);
+        }
+        return hx_part<0>(s, x, xs);
+    }
+};
+
+// ----------------------------------------------------------------------------
 // CSR view of a real symmetric matrix (val in the vector's scalar precision).
 // ----------------------------------------------------------------------------
 struct CsrView {
@@ -137,7 +173,7 @@ struct CsrView {
 // Library-side operator object (host).
 // ----------------------------------------------------------------------------
 struct msb_op {
-    int kind = 0;                // 0 Hubbard, 1 CSR
+    int kind = 0;                // 0 Hubbard, 1 CSR, 2 direct sum of Hubbard operators
     int64_t dim = 0;
     // Hubbard
     msb_model model{};
@@ -155,16 +191,19 @@ struct msb_op {
     msb::DevBuf<double> val64;
     msb::DevBuf<float> val32;
     msb::CsrView csr{};
+    // direct sum (parts are not owned: the caller keeps them alive)
+    std::vector<const msb_op*> parts;
+    msb::SumView sum{};
     int device = 0;
     double offdiag = 0;          // off-diagonal entries (hops, or CSR nonzeros)
 
     // Floating-point operations of one application (A x)[all s] on complex
     // vectors: two adds per hop plus the diagonal and hopping scale (Hubbard),
     // or a complex-by-real multiply-add per nonzero (CSR).  Halve for real vectors.
-    double hx_flops() const { return kind == 0 ? 2.0 * offdiag + 6.0 * double(dim) : 4.0 * offdiag; }
+    double hx_flops() const { return kind != 1 ? 2.0 * offdiag + 6.0 * double(dim) : 4.0 * offdiag; }
     // Bytes of the matrix itself read by one application (zero when matrix-free).
     double matrix_bytes(size_t csz) const {
-        return kind == 0 ? 0.0 : offdiag * (4.0 + (csz == 16 ? 8.0 : 4.0)) + double(dim + 1) * 8.0;
+        return kind != 1 ? 0.0 : offdiag * (4.0 + (csz == 16 ? 8.0 : 4.0)) + double(dim + 1) * 8.0;
     }
 };
 

@@ -372,6 +372,177 @@ static void rixs_map_sites_impl(const msb_model& m, const msb_map_params& prm, c
     if (maxit_hit) fail(MSB_EMAXITER, "some incident energies did not converge (maps written)");
 }
 
+// Maps of several independent clusters (uneven sizes) in one solve and one
+// continued fraction.  The direct sum A = (+)_c (H'_c - E_G,c) makes the seed
+// system (A - w_seed - i Gamma) carry each cluster's own energy origin while the
+// shifts w_in - w_seed stay common, so one Krylov recurrence (Alg. 1) on the
+// concatenated right-hand side (O2 |G_c>)_c solves every cluster and every
+// incident energy: the block-diagonal A keeps the clusters' components apart.
+// ||r_c|| <= ||r||, so the joint bound tol * min_c ||b_c|| meets each cluster's.
+static void rixs_map_clusters_impl(const msb_model* models, int nc, const msb_map_params& prm, const double* w_in,
+                                   int n_in, const double* w, int n_w, double* I_out, double* E_out,
+                                   msb_solve_info& info, cudaStream_t st) {
+    MSB_REQUIRE(models != nullptr && nc >= 1 && nc <= kMaxParts, "need 1..4 clusters");
+    MSB_REQUIRE(n_in >= 1 && n_in <= kMaxShifts && int64_t(nc) * n_in <= 65535,
+                "n_clusters * n_in must be at most 65535 (and n_in at most 4096)");
+    MSB_REQUIRE(w_in && w && I_out && n_w >= 1, "NULL argument");
+    MSB_REQUIRE(prm.Gamma > 0 && prm.eta > 0, "Gamma and eta must be > 0");
+    MSB_REQUIRE(prm.precision == MSB_FP64 || prm.precision == MSB_FP32_MIXED, "unknown precision");
+    for (int c = 0; c < nc; ++c) {
+        validate_model(models[c]);
+        MSB_REQUIRE(models[c].n_up + 1 <= models[c].L, "the intermediate sector needs n_up + 1 <= L");
+        MSB_REQUIRE(models[c].core_site >= 0 && models[c].core_site < models[c].L, "core_site out of range");
+    }
+    const auto t_start = std::chrono::steady_clock::now();
+    auto secs = [](std::chrono::steady_clock::time_point a) {
+        return std::chrono::duration<double>(std::chrono::steady_clock::now() - a).count();
+    };
+    int64_t launches = 0;
+    std::vector<std::unique_ptr<msb_op>> opH(nc), opHp(nc);
+    for (int c = 0; c < nc; ++c) {
+        msb_op* a = nullptr;
+        msb_status s1 = msb_op_create_hubbard(&models[c], 0, &a);
+        if (s1 != MSB_OK) fail(s1, msb_last_error());
+        opH[c].reset(a);
+        s1 = msb_op_create_hubbard(&models[c], 1, &a);
+        if (s1 != MSB_OK) fail(s1, msb_last_error());
+        opHp[c].reset(a);
+    }
+    // ground states, one per cluster
+    auto t0 = std::chrono::steady_clock::now();
+    std::vector<DevBuf<double>> G(nc);
+    std::vector<double> EG(nc);
+    for (int c = 0; c < nc; ++c) {
+        G[c].alloc(opH[c]->dim);
+        GroundResult gr;
+        ground_state(opH[c].get(), prm.gs_tol, prm.gs_maxit, nullptr, G[c].p, gr, st);
+        if (gr.status != MSB_OK) fail(gr.status, "ground state: tolerance not reached");
+        EG[c] = gr.E;
+        info.gs_residual = std::max(info.gs_residual, gr.residual);
+        info.matvecs += gr.matvecs;
+        launches += gr.launches;
+        if (E_out) E_out[c] = gr.E;
+    }
+    info.E_G = EG[0];
+    info.seconds_ground_state = secs(t0);
+
+    // concatenated right-hand side (O2 |G_c>)_c and its per-cluster norms
+    t0 = std::chrono::steady_clock::now();
+    const size_t csz = prm.precision == MSB_FP64 ? sizeof(double2) : sizeof(float2);
+    std::vector<int64_t> offp(nc + 1, 0);
+    for (int c = 0; c < nc; ++c) offp[c + 1] = offp[c] + opHp[c]->dim;
+    const int64_t n = offp[nc];
+    DevBuf<char> Ebuf(size_t(n) * csz);
+    double bmin = 0, b2 = 0;
+    for (int c = 0; c < nc; ++c) {
+        const msb_model& m = models[c];
+        const int64_t D = opH[c]->dim, Ddn = opH[c]->hub.Ddn;
+        auto map = cdag_rowmap(m.L, m.n_up, m.core_site);
+        char* dst = Ebuf.p + size_t(offp[c]) * csz;
+        if (prm.precision == MSB_FP64)
+            launch_rowmap(G[c].p, (double2*)dst, map, Ddn, D, opHp[c]->dim, 1, st, launches);
+        else
+            launch_rowmap(G[c].p, (float2*)dst, map, Ddn, D, opHp[c]->dim, 1, st, launches);
+        std::vector<double> hg(D);
+        MSB_CUDA(cudaMemcpyAsync(hg.data(), G[c].p, D * sizeof(double), cudaMemcpyDeviceToHost, st));
+        MSB_CUDA(cudaStreamSynchronize(st));
+        double nb = 0;
+        for (size_t r = 0; r < map.size(); ++r) {
+            if (map[r] < 0) continue;
+            const double* g = hg.data() + int64_t(map[r] >> 1) * Ddn;
+            for (int64_t d = 0; d < Ddn; ++d) nb += g[d] * g[d];
+        }
+        MSB_REQUIRE(nb > 0, "O2 annihilates the ground state of a cluster (no intermediate state)");
+        bmin = c == 0 ? std::sqrt(nb) : std::min(bmin, std::sqrt(nb));
+        b2 += nb;
+    }
+    // the direct sum and the joint solve
+    std::vector<const msb_op*> parts(nc);
+    std::vector<double> shifts(nc);
+    for (int c = 0; c < nc; ++c) { parts[c] = opHp[c].get(); shifts[c] = -EG[c]; }
+    std::unique_ptr<msb_op> A;
+    {
+        msb_op* a = nullptr;
+        const msb_status s1 = msb_op_create_direct_sum(parts.data(), shifts.data(), nc, &a);
+        if (s1 != MSB_OK) fail(s1, msb_last_error());
+        A.reset(a);
+    }
+    int s0 = prm.seed_index;
+    if (s0 < 0) {
+        s0 = 0;
+        for (int k = 1; k < n_in; ++k) if (std::fabs(w_in[k]) < std::fabs(w_in[s0])) s0 = k;
+    }
+    MSB_REQUIRE(s0 < n_in, "seed_index out of range");
+    SolveProblem pr;
+    pr.n = n;
+    pr.ns = n_in;
+    pr.b = Ebuf.p;
+    pr.n_out = n;
+    pr.c0 = make_double2(-w_in[s0], -prm.Gamma);
+    pr.tol = prm.solve_tol * bmin / std::sqrt(b2);
+    pr.maxit = prm.maxit;
+    pr.block = pick_block(prm.block, prm.precision);
+    pr.prec = prm.precision;
+    pr.shifts.resize(n_in);
+    for (int k = 0; k < n_in; ++k) pr.shifts[k] = make_double2(w_in[k] - w_in[s0], 0.0);
+    DevBuf<char> X(size_t(n_in) * n * csz);
+    pr.x = X.p;
+    SolveResult sr;
+    multishift_solve(A.get(), pr, sr, st);
+    MSB_CUDA(cudaStreamSynchronize(st));
+    launches += sr.launches;
+    info.iterations = sr.iterations;
+    info.n_converged = sr.n_converged;
+    info.flushes = sr.flushes;
+    info.seed_residual = sr.seed_residual;
+    for (double r : sr.resid) info.max_shift_residual = std::max(info.max_shift_residual, r);
+    info.matvecs += sr.iterations;
+    if (sr.status != MSB_OK && sr.status != MSB_EMAXITER) fail(sr.status, "multi-shift solve failed");
+    Ebuf.release();
+    // phi_{c,k} = O1 Psi_{c,k}, column c * n_in + k, stride ldphi
+    int64_t ldphi = 0;
+    for (int c = 0; c < nc; ++c) ldphi = std::max(ldphi, opH[c]->dim);
+    DevBuf<char> Phi(size_t(nc) * n_in * ldphi * csz);
+    for (int c = 0; c < nc; ++c) {
+        const msb_model& m = models[c];
+        auto omap = c_rowmap(m.L, m.n_up, m.core_site);
+        const int64_t Ddn = opH[c]->hub.Ddn;
+        const char* src = X.p + size_t(offp[c]) * csz;
+        char* dst = Phi.p + size_t(c) * n_in * ldphi * csz;
+        if (prm.precision == MSB_FP64)
+            launch_rowmap((const double2*)src, (double2*)dst, omap, Ddn, n, ldphi, n_in, st, launches);
+        else
+            launch_rowmap((const float2*)src, (float2*)dst, omap, Ddn, n, ldphi, n_in, st, launches);
+    }
+    X.release();
+    info.seconds_solve = secs(t0);
+    // one continued fraction over every cluster's columns
+    t0 = std::chrono::steady_clock::now();
+    CFColumns P;
+    P.phi = Phi.p;
+    P.ldphi = ldphi;
+    P.nv = nc * n_in;
+    for (int c = 0; c < nc; ++c) P.ops.push_back(opH[c].get());
+    for (int c = 0; c < nc; ++c)
+        for (int k = 0; k < n_in; ++k) {
+            P.q.push_back(c);
+            P.E0.push_back(EG[c]);
+        }
+    CFResult cr;
+    continued_fraction_columns(P, w, n_w, prm.eta, prm.cf_tol, prm.cf_check, prm.cf_maxdepth, prm.precision, I_out,
+                               cr, st);
+    launches += cr.launches;
+    info.matvecs += cr.matvecs;
+    int dmax = 0, dmin = 1 << 30;
+    for (int d : cr.depth) { dmax = std::max(dmax, d); dmin = std::min(dmin, d); }
+    info.cf_depth_max = dmax;
+    info.cf_depth_min = dmin;
+    info.seconds_second_step = secs(t0);
+    info.seconds_total = secs(t_start);
+    info.kernel_launches = launches;
+    if (sr.status == MSB_EMAXITER) fail(MSB_EMAXITER, "some incident energies did not converge (maps written)");
+}
+
 }  // namespace msb
 
 static bool same_model(const msb_model& a, const msb_model& b) {
@@ -437,6 +608,26 @@ extern "C" msb_status msb_rixs_map(const msb_model* model, const msb_map_params*
             ~Fill() { if (dst) { src->device_bytes = msb::g_alloc_bytes; *dst = *src; } }
         } fill{info, &local};
         msb::rixs_map(*model, *params, G, E_G, w_in, n_in, w, n_w, I_out, local, scope.s);
+        scope.finish();
+        msb::prof_collect();
+    });
+}
+
+extern "C" msb_status msb_rixs_map_clusters(const msb_model* models, int n_clusters, const msb_map_params* params,
+                                            const double* w_in, int n_in, const double* w, int n_w, double* I_out,
+                                            double* E_G_out, msb_solve_info* info, void* stream) {
+    if (info) *info = msb_solve_info{};
+    return msb::guard("msb_rixs_map_clusters", [&] {
+        msb::require_device();
+        MSB_REQUIRE(models != nullptr && params != nullptr, "NULL argument");
+        msb::g_alloc_bytes = 0;
+        msb_solve_info local{};
+        msb::StreamScope scope((cudaStream_t)stream);
+        struct Fill {
+            msb_solve_info* dst; msb_solve_info* src;
+            ~Fill() { if (dst) { src->device_bytes = msb::g_alloc_bytes; *dst = *src; } }
+        } fill{info, &local};
+        msb::rixs_map_clusters_impl(models, n_clusters, *params, w_in, n_in, w, n_w, I_out, E_G_out, local, scope.s);
         scope.finish();
         msb::prof_collect();
     });

@@ -68,6 +68,7 @@ SIGNATURES = {
     "msb_basis_destroy": (None, [_P]),
     "msb_op_create_hubbard": (_I, [C.POINTER(msb_model), _I, C.POINTER(_P)]),
     "msb_op_create_csr": (_I, [_I64, C.POINTER(C.c_int64), C.POINTER(C.c_int32), _PD, C.POINTER(_P)]),
+    "msb_op_create_direct_sum": (_I, [C.POINTER(_P), _PD, _I, C.POINTER(_P)]),
     "msb_op_dim": (_I, [_P, C.POINTER(_I64)]),
     "msb_op_destroy": (None, [_P]),
     "msb_op_apply": (_I, [_P, msb_complex, _P, _P, _I, _I, _P]),
@@ -84,6 +85,8 @@ SIGNATURES = {
                               C.POINTER(msb_solve_info), _P]),
     "msb_rixs_map_sites": (_I, [C.POINTER(msb_model), C.POINTER(msb_map_params), C.POINTER(C.c_int), _I, _PD, _I,
                                 _PD, _I, _PD, C.POINTER(msb_solve_info), _P]),
+    "msb_rixs_map_clusters": (_I, [C.POINTER(msb_model), _I, C.POINTER(msb_map_params), _PD, _I, _PD, _I, _PD,
+                                   _PD, C.POINTER(msb_solve_info), _P]),
     "msb_profile_enable": (None, [_I]),
     "msb_profile_reset": (None, []),
     "msb_profile_read": (_I, [C.POINTER(msb_kernel_stat), _I]),
