@@ -41,6 +41,44 @@ __device__ __forceinline__ void df_add_prod(float& hi, float& lo, float x, float
 }
 __device__ __forceinline__ double df_value(float hi, float lo) { return double(hi) + double(lo); }
 
+// (hi, lo) += (bh, bl) in float-float arithmetic (TwoSum of the high parts).
+__device__ __forceinline__ void df_add(float& hi, float& lo, float bh, float bl) {
+    const float s = __fadd_rn(hi, bh);
+    const float bb = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(bh, bb));
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(e, bl));
+}
+
+// Block sum of per-thread float-float pairs with FP32 arithmetic only (warp
+// shuffles, then one warp over the warp sums); thread 0 gets hi + lo as a
+// double.  sm: 64 floats.  Every thread of the block must call it.
+__device__ __forceinline__ double block_sum_df(float hi, float lo, float* sm) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, hi, o), ol = __shfl_xor_sync(0xffffffffu, lo, o);
+        df_add(hi, lo, oh, ol);
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    if (lane == 0) {
+        sm[2 * wid] = hi;
+        sm[2 * wid + 1] = lo;
+    }
+    __syncthreads();
+    double r = 0.0;
+    if (wid == 0) {
+        hi = lane < nw ? sm[2 * lane] : 0.f;
+        lo = lane < nw ? sm[2 * lane + 1] : 0.f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float oh = __shfl_xor_sync(0xffffffffu, hi, o), ol = __shfl_xor_sync(0xffffffffu, lo, o);
+            df_add(hi, lo, oh, ol);
+        }
+        r = double(hi) + double(lo);
+    }
+    return r;
+}
+
 // Compensated accumulators of a bilinear product (re, im) and a squared norm.
 struct DF4 { float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f, nh = 0.f, nl = 0.f; };
 __device__ __forceinline__ void bil_acc_df(float2 u, float2 v, DF4& a) {

@@ -446,6 +446,9 @@ struct CFCoef {
     double* sig;      // sig_k per column
     double* cB;       // b_k sig_{k-1} per column (0 at k = 0)
     double* cC;       // a_k sig_k per column
+    float* sigf;      // the same three rounded to FP32, for the FP32 kernels
+    float* cBf;
+    float* cCf;
 };
 
 constexpr int kMaxHops = 16;
@@ -477,20 +480,23 @@ __global__ void __launch_bounds__(256, 6) k_cf_apply_hub(HubView h0, const HubVi
     S* lut = reinterpret_cast<S*>(row + h.Ddn);                     // 3 (L + 1) diagonal values * sig
     __shared__ int s_uoff[kMaxHops];
     __shared__ S s_usg[kMaxHops];
-    __shared__ double red[32];
+    __shared__ double red[32];                                      // 64 floats in the FP32 path
     const int Ddn = int(h.Ddn);
     const C* __restrict__ Vc = Vk + int64_t(c) * ld;
     const C* __restrict__ Pc = Vkm1 + int64_t(c) * ld;
     C* __restrict__ Wc = W + int64_t(c) * ld;
     const int rbase = u * Ddn;
-    const double sig = cf.sig[c], cB = cf.cB[c];
-    const bool has_prev = cB != 0.0;
+    constexpr bool f32 = std::is_same<S, float>::value;
+    const S sig = f32 ? S(cf.sigf[c]) : S(cf.sig[c]);
+    const S cB = f32 ? S(cf.cBf[c]) : S(cf.cB[c]);
+    const bool has_prev = cB != S(0);
     const uint32_t su = __ldg(h.sup + u);
     const int nu = __ldg(h.nup + u);
     for (int d = threadIdx.x; d < Ddn; d += blockDim.x) row[d] = Vc[rbase + d];
     for (int i = threadIdx.x; i < 3 * (L + 1); i += blockDim.x) {
         const int p = i % (L + 1), nb = i / (L + 1);
-        lut[i] = S(sig * (h.U * double(p) - h.Uc * double(nb)));
+        if constexpr (f32) lut[i] = sig * (h.Uf * float(p) - h.Ucf * float(nb));
+        else lut[i] = sig * (h.U * double(p) - h.Uc * double(nb));
     }
     if (threadIdx.x < nu) {
         const int32_t ent = __ldg(h.hup + int64_t(threadIdx.x) * h.Dup + u);
@@ -500,8 +506,8 @@ __global__ void __launch_bounds__(256, 6) k_cf_apply_hub(HubView h0, const HubVi
     __syncthreads();
     const int core = h.core;
     const int ubits = core >= 0 ? int((su >> core) & 1u) : 0;
-    const S mt = S(-h.t * sig);
-    const S mcB = S(-cB);
+    const S mt = f32 ? S(-h.tf * sig) : S(-h.t * sig);
+    const S mcB = -cB;
     double dot = 0.0;
     float dhi = 0.f, dlo = 0.f;
     for (int d = threadIdx.x; d < Ddn; d += blockDim.x) {
@@ -570,10 +576,14 @@ __global__ void __launch_bounds__(256, 6) k_cf_apply_hub(HubView h0, const HubVi
             dot = fma(x.x, wv.x, fma(x.y, wv.y, dot));
         }
     }
-    if constexpr (std::is_same<S, float>::value) dot = df_value(dhi, dlo);
-    double acc[1] = {dot};
-    block_sum<1>(acc, red);
-    if (threadIdx.x == 0) part[int64_t(blockIdx.y) * gridDim.x + blockIdx.x] = acc[0];
+    if constexpr (f32) {
+        const double tot = block_sum_df(dhi, dlo, reinterpret_cast<float*>(red));
+        if (threadIdx.x == 0) part[int64_t(blockIdx.y) * gridDim.x + blockIdx.x] = tot;
+    } else {
+        double acc[1] = {dot};
+        block_sum<1>(acc, red);
+        if (threadIdx.x == 0) part[int64_t(blockIdx.y) * gridDim.x + blockIdx.x] = acc[0];
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -596,7 +606,9 @@ __global__ void __launch_bounds__(256, 6) k_cf_apply_hub(HubView h0, const HubVi
 __device__ __forceinline__ long long fx_term(double v, int eB, long long neg) {
     const long long b = __double_as_longlong(v);
     const int e = int(static_cast<unsigned>(b >> 52) & 0x7FFu);
-    const int r = e == 0 ? 63 : min(max(eB - e, 0), 63);       // zero / subnormal -> 0
+    // eB >= 63, so zero and subnormals (e = 0) shift out entirely; a non-finite
+    // component (e > eB) also maps to 0 here and reaches W through the diagonal.
+    const unsigned r = min(static_cast<unsigned>(eB - e), 63u);
     const unsigned long long m =
         ((static_cast<unsigned long long>(b) & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull) << 5;
     const long long f = static_cast<long long>(m >> r);
@@ -607,7 +619,7 @@ __device__ __forceinline__ long long fx_term(double v, int eB, long long neg) {
 __device__ __forceinline__ long long fx_signed(long long f, long long neg) { return (f ^ neg) - neg; }
 
 template <bool Multi>
-__global__ void __launch_bounds__(256, 4) k_cf_apply_hub_fx(HubView h0, const HubView* __restrict__ hv,
+__global__ void __launch_bounds__(256, 5) k_cf_apply_hub_fx(HubView h0, const HubView* __restrict__ hv,
                                                             const int* __restrict__ colq,
                                                             const double2* __restrict__ Vk,
                                                             const double2* __restrict__ Vkm1,
@@ -636,7 +648,7 @@ __global__ void __launch_bounds__(256, 4) k_cf_apply_hub_fx(HubView h0, const Hu
     const double sig = cf.sig[c], cB = cf.cB[c];
     const bool has_prev = (__double_as_longlong(cB) << 1) != 0;
     const int es = int(static_cast<unsigned long long>(__double_as_longlong(sig)) >> 52) & 0x7FF;
-    const int eB = min(2047 - es, 2100);
+    const int eB = max(min(2047 - es, 2100), 63);
     const uint32_t su = __ldg(h.sup + u);
     const int nu = __ldg(h.nup + u);
     for (int d = threadIdx.x; d < Ddn; d += blockDim.x) {
@@ -658,6 +670,7 @@ __global__ void __launch_bounds__(256, 4) k_cf_apply_hub_fx(HubView h0, const Hu
     // -t sig times the fixed-point unit 2^(eB - 1080) (an exact power of two)
     const double mts = (-h.t * sig) * __longlong_as_double(static_cast<long long>(eB - 57) << 52);
     const double mcB = -cB;
+    const uint16_t* __restrict__ t16 = h.hdn16;                     // [slot][state], (target << 1) | neg
     double dot = 0.0;
     for (int d = threadIdx.x; d < Ddn; d += blockDim.x) {
         long long ax = 0, ay = 0;
@@ -684,8 +697,8 @@ __global__ void __launch_bounds__(256, 4) k_cf_apply_hub_fx(HubView h0, const Hu
         const int nd = __ldg(h.ndn + d);
         e = 0;
         for (; e + 4 <= nd; e += 4) {
-            const int32_t h0 = __ldg(h.hdn + e * Ddn + d), h1 = __ldg(h.hdn + (e + 1) * Ddn + d);
-            const int32_t h2 = __ldg(h.hdn + (e + 2) * Ddn + d), h3 = __ldg(h.hdn + (e + 3) * Ddn + d);
+            const int h0 = __ldg(t16 + e * Ddn + d), h1 = __ldg(t16 + (e + 1) * Ddn + d);
+            const int h2 = __ldg(t16 + (e + 2) * Ddn + d), h3 = __ldg(t16 + (e + 3) * Ddn + d);
             const longlong2 f0 = row[h0 >> 1], f1 = row[h1 >> 1], f2 = row[h2 >> 1], f3 = row[h3 >> 1];
             const long long g0 = -(h0 & 1), g1 = -(h1 & 1), g2 = -(h2 & 1), g3 = -(h3 & 1);
             ax += fx_signed(f0.x, g0);
@@ -698,7 +711,7 @@ __global__ void __launch_bounds__(256, 4) k_cf_apply_hub_fx(HubView h0, const Hu
             ay += fx_signed(f3.y, g3);
         }
         for (; e < nd; ++e) {
-            const int32_t hh = __ldg(h.hdn + e * Ddn + d);
+            const int hh = __ldg(t16 + e * Ddn + d);
             const longlong2 f = row[hh >> 1];
             const long long g = -(hh & 1);
             ax += fx_signed(f.x, g);
@@ -749,15 +762,15 @@ __global__ void __launch_bounds__(256, 6) k_cf_apply_hub_f2x2(HubView h0, const 
     float* lut = reinterpret_cast<float*>(row + h.Ddn);             // 3 (L + 1) diagonal values * sig
     __shared__ int s_uoff[kMaxHops];
     __shared__ float s_usg[kMaxHops];
-    __shared__ double red[32];
+    __shared__ float red[64];
     const int Ddn = int(h.Ddn);
     const int half = Ddn >> 1;
     const float2* __restrict__ Vc = Vk + int64_t(c) * ld;
     const float4* __restrict__ Pc4 = reinterpret_cast<const float4*>(Vkm1 + int64_t(c) * ld);
     float4* __restrict__ Wc4 = reinterpret_cast<float4*>(W + int64_t(c) * ld);
     const int rbase = u * Ddn;                      // even
-    const double sig = cf.sig[c], cB = cf.cB[c];
-    const bool has_prev = cB != 0.0;
+    const float sig = cf.sigf[c], cB = cf.cBf[c];
+    const bool has_prev = cB != 0.f;
     const uint32_t su = __ldg(h.sup + u);
     const int nu = __ldg(h.nup + u);
     {
@@ -767,7 +780,7 @@ __global__ void __launch_bounds__(256, 6) k_cf_apply_hub_f2x2(HubView h0, const 
     }
     for (int i = threadIdx.x; i < 3 * (L + 1); i += blockDim.x) {
         const int p = i % (L + 1), nb = i / (L + 1);
-        lut[i] = float(sig * (h.U * double(p) - h.Uc * double(nb)));
+        lut[i] = sig * (h.Uf * float(p) - h.Ucf * float(nb));
     }
     if (threadIdx.x < nu) {
         const int32_t ent = __ldg(h.hup + int64_t(threadIdx.x) * h.Dup + u);
@@ -777,8 +790,8 @@ __global__ void __launch_bounds__(256, 6) k_cf_apply_hub_f2x2(HubView h0, const 
     __syncthreads();
     const int core = h.core;
     const int ubits = core >= 0 ? int((su >> core) & 1u) : 0;
-    const float mt = float(-h.t * sig);
-    const float mcB = float(-cB);
+    const float mt = -h.tf * sig;
+    const float mcB = -cB;
     const float4* __restrict__ Vc4 = reinterpret_cast<const float4*>(Vc);
     const uint32_t* __restrict__ t32 = reinterpret_cast<const uint32_t*>(h.hdn16);
     const uint16_t* __restrict__ n16 = reinterpret_cast<const uint16_t*>(h.ndn);
@@ -843,9 +856,8 @@ __global__ void __launch_bounds__(256, 6) k_cf_apply_hub_f2x2(HubView h0, const 
         df_add_prod(dhi, dlo, x1.x, wv.z);
         df_add_prod(dhi, dlo, x1.y, wv.w);
     }
-    double acc[1] = {df_value(dhi, dlo)};
-    block_sum<1>(acc, red);
-    if (threadIdx.x == 0) part[int64_t(blockIdx.y) * gridDim.x + blockIdx.x] = acc[0];
+    const double tot = block_sum_df(dhi, dlo, red);
+    if (threadIdx.x == 0) part[int64_t(blockIdx.y) * gridDim.x + blockIdx.x] = tot;
 }
 
 // Pass A for any operator view (CSR): flat grid over elements.
@@ -894,6 +906,7 @@ __global__ void k_cf_reduce_a(const double* part, int nblk, const int* cols, dou
         const double a = cf.sig[c] * v[0];
         astore[int64_t(k) * stride_k + c] = a;
         cf.cC[c] = a * cf.sig[c];
+        cf.cCf[c] = float(cf.cC[c]);
     }
 }
 
@@ -928,7 +941,7 @@ __global__ void __launch_bounds__(256) k_cf_orth(const C* __restrict__ Vk, C* __
     const V16* __restrict__ v4 = reinterpret_cast<const V16*>(Vk + int64_t(c) * ld);
     V16* __restrict__ w4 = reinterpret_cast<V16*>(W + int64_t(c) * ld);
     const int64_t nv = clen[c] / per;                 // column length, rounded up to even
-    const S mc = S(-cf.cC[c]);
+    const S mc = std::is_same<S, float>::value ? S(-cf.cCf[c]) : S(-cf.cC[c]);
     double acc = 0.0;
     float hi = 0.f, lo = 0.f;
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
@@ -946,9 +959,13 @@ __global__ void __launch_bounds__(256) k_cf_orth(const C* __restrict__ Vk, C* __
         orth_step(v4[i], x0, mc, acc, hi, lo);
         w4[i] = x0;
     }
-    if constexpr (std::is_same<S, float>::value) acc = df_value(hi, lo);
-    double a1[1] = {acc};
-    store_partials<1>(a1, sm, part);
+    if constexpr (std::is_same<S, float>::value) {
+        const double tot = block_sum_df(hi, lo, reinterpret_cast<float*>(sm));
+        if (threadIdx.x == 0) part[int64_t(blockIdx.y) * gridDim.x + blockIdx.x] = tot;
+    } else {
+        double a1[1] = {acc};
+        store_partials<1>(a1, sm, part);
+    }
 }
 
 // b_{k+1} = ||W||; next step: cB = b_{k+1} sig_k, sig = 1 / b_{k+1}.
@@ -963,6 +980,8 @@ __global__ void k_cf_reduce_b(const double* part, int nblk, const int* cols, dou
         bstore[int64_t(k) * stride_k + c] = b;
         cf.cB[c] = b * cf.sig[c];
         cf.sig[c] = b > 0.0 ? 1.0 / b : 0.0;
+        cf.cBf[c] = float(cf.cB[c]);
+        cf.sigf[c] = float(cf.sig[c]);
     }
 }
 
@@ -1010,6 +1029,9 @@ __global__ void k_cf_setup(const double* part, int nblk, double* n0, CFCoef cf) 
         cf.sig[c] = v[0] > 0.0 ? 1.0 / sqrt(v[0]) : 0.0;
         cf.cB[c] = 0.0;
         cf.cC[c] = 0.0;
+        cf.sigf[c] = float(cf.sig[c]);
+        cf.cBf[c] = 0.f;
+        cf.cCf[c] = 0.f;
     }
 }
 
@@ -1030,7 +1052,7 @@ static void cf_impl(const CFColumns& P, const View& view, const double* w, int n
     const int per = int(16 / sizeof(C));
     const int grid = grid_for(ld / per, 256, 4);
     int64_t hub_smem = 0;
-    bool rows = false, pair = false;
+    bool rows = false, pair = false, fx = false;
     int nblkA = grid;
     std::vector<HubView> hviews;
     if constexpr (hub) {
@@ -1038,6 +1060,7 @@ static void cf_impl(const CFColumns& P, const View& view, const double* w, int n
         int maxL = 0;
         rows = true;
         pair = std::is_same<C, float2>::value;
+        fx = std::is_same<C, double2>::value;
         for (const msb_op* o : P.ops) {
             const HubView& h = o->hub;
             hviews.push_back(h);
@@ -1046,13 +1069,14 @@ static void cf_impl(const CFColumns& P, const View& view, const double* w, int n
             maxL = std::max(maxL, h.L);
             rows = rows && h.Wup <= kMaxHops && h.Dup * h.Ddn < (int64_t(1) << 31);
             pair = pair && h.Ddn % 2 == 0 && h.hdn16 != nullptr;
+            fx = fx && h.hdn16 != nullptr;
         }
         hub_smem = maxDdn * int64_t(sizeof(C)) + 3 * (maxL + 1) * 8;
         rows = rows && hub_smem <= 160 * 1024;
         if (rows) {
             nblkA = int(maxDup);
             const void* fn = nullptr;
-            if (std::is_same<C, double2>::value)
+            if (fx)
                 fn = multi ? (const void*)k_cf_apply_hub_fx<true> : (const void*)k_cf_apply_hub_fx<false>;
             else if (pair)
                 fn = multi ? (const void*)k_cf_apply_hub_f2x2<true> : (const void*)k_cf_apply_hub_f2x2<false>;
@@ -1065,11 +1089,12 @@ static void cf_impl(const CFColumns& P, const View& view, const double* w, int n
     DevBuf<C> Q(3 * size_t(nv) * ld);
     DevBuf<double> part(size_t(std::max(grid, nblkA)) * nv), a(size_t(maxdepth) * nv), b(size_t(maxdepth) * nv),
         n0(nv), sig(nv), cB(nv), cC(nv), I(size_t(nv) * n_w), diff(2 * size_t(nv)), wdev(n_w), E0d(nv);
+    DevBuf<float> sigf(nv), cBf(nv), cCf(nv);
     DevBuf<int> cols(nv), depth(nv), colq(nv);
     DevBuf<int64_t> nlen_d(nv), clen_d(nv);
     DevBuf<HubView> hv(std::max<size_t>(1, hviews.size()));
     if (!hviews.empty()) hv.upload(hviews.data(), hviews.size(), st);
-    CFCoef cf{sig.p, cB.p, cC.p};
+    CFCoef cf{sig.p, cB.p, cC.p, sigf.p, cBf.p, cCf.p};
     wdev.upload(w, n_w, st);
     E0d.upload(P.E0.data(), nv, st);
     colq.upload(P.q.data(), nv, st);
@@ -1117,7 +1142,7 @@ static void cf_impl(const CFColumns& P, const View& view, const double* w, int n
             bool done_hub = false;
             if constexpr (hub) {
                 const dim3 g(gridA.x, unsigned(nact));
-                if (rows && std::is_same<C, double2>::value) {
+                if (rows && fx) {
                     auto x = reinterpret_cast<const double2*>(vk);
                     auto xm = reinterpret_cast<const double2*>(vkm1);
                     auto y = reinterpret_cast<double2*>(wv);

@@ -47,6 +47,7 @@ static void build_hubbard(msb_op* op, const msb_model& m, int intermediate) {
     h.hdn16 = op->hdn16.p;
     h.sup = op->sup.p; h.sdn = op->sdn.p;
     h.t = m.t; h.U = m.U; h.Uc = m.Uc;
+    h.tf = float(m.t); h.Uf = float(m.U); h.Ucf = float(m.Uc);
     h.core = intermediate ? m.core_site : -1;
     h.L = m.L;
     op->dim = h.Dup * h.Ddn;

@@ -69,6 +69,7 @@ struct HubView {
     double t, U, Uc;
     int core;              // core-hole site, -1: none (plain H)
     int L;                 // sites
+    float tf, Uf, Ucf;     // t, U, Uc rounded to FP32 (FP32 kernels use no FP64 arithmetic)
 
     // U popc(u & d) - Uc (n_{j,up} + n_{j,dn}), in the vector's precision (no
     // FP64 work in the FP32 path).
