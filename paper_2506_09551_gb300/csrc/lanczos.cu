@@ -386,34 +386,57 @@ void ground_state(msb_op* H, double tol, int maxit, const double* start, double*
 
 // ---------------------------------------------------------------------------
 // Continued fraction: I(w) = -(1/pi) Im G(E0 + w + i eta),
-// G(z) = n0 / (z - a_0 - b_1^2 / (z - a_1 - ...)), evaluated bottom-up with a
-// zero tail (Eq. 1 with the paper's continued-fraction expansion).
+// G(z) = n0 / (z - a_0 - b_1^2 / (z - a_1 - ...)) cut after level k_to with a
+// zero tail (Eq. 1 with the paper's continued-fraction expansion).  The K-th
+// convergent is carried forward: each call folds in levels [k_from, k_to) and
+// keeps the recurrence state per (column, w), so a run of K levels costs O(K)
+// per point instead of O(K^2 / check) for bottom-up re-evaluation at every check.
 // One CTA per active column; threads over w.  Also reports the column's
 // max |I_new - I_old| and max |I_new|.
 // ---------------------------------------------------------------------------
 __global__ void k_cf_eval(const double* __restrict__ a, const double* __restrict__ b, int64_t stride_k,
-                          const double* __restrict__ n0, const int* __restrict__ cols, const int* __restrict__ depth,
+                          const double* __restrict__ n0, const int* __restrict__ cols, int k_from, int k_to,
                           const double* __restrict__ E0c, const double* __restrict__ w, int n_w, double eta,
+                          double2* __restrict__ gst, double2* __restrict__ Cst, double2* __restrict__ Dst,
                           double* I, double* diff) {
     __shared__ double sm[2 * 32];
     const int c = cols[blockIdx.x];
     const double E0 = E0c[c];
-    const int K = depth[c];
     double dmax = 0.0, imax = 0.0;
     for (int i = threadIdx.x; i < n_w; i += blockDim.x) {
         const double2 z = make_double2(E0 + w[i], eta);
-        double2 g = make_double2(0.0, 0.0);
-        for (int k = K - 1; k >= 0; --k) {
-            const double ak = a[int64_t(k) * stride_k + c];
-            double2 den = make_double2(z.x - ak, z.y);
-            if (k < K - 1) {
-                const double bk = b[int64_t(k) * stride_k + c];
-                den = csub(den, make_double2(bk * bk * g.x, bk * bk * g.y));
-            }
-            g = cdiv(make_double2(1.0, 0.0), den);
-        }
-        const double val = K > 0 ? -(n0[c] * g.y) / M_PI : 0.0;
         const int64_t o = int64_t(c) * n_w + i;
+        // g = d_0 + c_1 / (d_1 + c_2 / (d_2 + ...)), d_j = z - a_j, c_j = -b_j^2, by the
+        // modified Lentz recurrences C_j = d_j + c_j / C_{j-1}, D_j = 1 / (d_j + c_j D_{j-1}),
+        // g_j = g_{j-1} C_j D_j; G = 1 / g.  For Im z > 0 every C_j and 1 / D_j has
+        // imaginary part >= eta, so no division by zero.
+        double2 g, C, D;
+        int j = k_from;
+        if (j == 0) {
+            g = make_double2(z.x - a[c], z.y);
+            C = g;
+            D = make_double2(0.0, 0.0);
+            j = 1;
+        } else {
+            g = gst[o];
+            C = Cst[o];
+            D = Dst[o];
+        }
+        for (; j < k_to; ++j) {
+            const double aj = a[int64_t(j) * stride_k + c];
+            const double bj = b[int64_t(j - 1) * stride_k + c];
+            const double cj = -bj * bj;
+            const double2 d = make_double2(z.x - aj, z.y);
+            D = cdiv(make_double2(1.0, 0.0), make_double2(fma(cj, D.x, d.x), fma(cj, D.y, d.y)));
+            const double2 ic = cdiv(make_double2(1.0, 0.0), C);
+            C = make_double2(fma(cj, ic.x, d.x), fma(cj, ic.y, d.y));
+            g = cmul(g, cmul(C, D));
+        }
+        gst[o] = g;
+        Cst[o] = C;
+        Dst[o] = D;
+        const double2 G = cdiv(make_double2(1.0, 0.0), g);
+        const double val = k_to > 0 ? -(n0[c] * G.y) / M_PI : 0.0;
         dmax = fmax(dmax, fabs(val - I[o]));
         imax = fmax(imax, fabs(val));
         I[o] = val;
@@ -1090,7 +1113,9 @@ static void cf_impl(const CFColumns& P, const View& view, const double* w, int n
     DevBuf<double> part(size_t(std::max(grid, nblkA)) * nv), a(size_t(maxdepth) * nv), b(size_t(maxdepth) * nv),
         n0(nv), sig(nv), cB(nv), cC(nv), I(size_t(nv) * n_w), diff(2 * size_t(nv)), wdev(n_w), E0d(nv);
     DevBuf<float> sigf(nv), cBf(nv), cCf(nv);
-    DevBuf<int> cols(nv), depth(nv), colq(nv);
+    DevBuf<double2> gst(size_t(nv) * n_w), Cst(size_t(nv) * n_w), Dst(size_t(nv) * n_w);
+    int k_eval = 0;                      // levels already folded into the convergents
+    DevBuf<int> cols(nv), colq(nv);
     DevBuf<int64_t> nlen_d(nv), clen_d(nv);
     DevBuf<HubView> hv(std::max<size_t>(1, hviews.size()));
     if (!hviews.empty()) hv.upload(hviews.data(), hviews.size(), st);
@@ -1201,11 +1226,11 @@ static void cf_impl(const CFColumns& P, const View& view, const double* w, int n
         ++k;
         if (k % check == 0 || k == maxdepth) {
             for (int i = 0; i < nact; ++i) hdepth[hcols[i]] = k;
-            depth.upload(hdepth.data(), nv, st);
             {
-                ProfScope ps("cf_eval", st, 0, 20.0 * nact * n_w * double(k));
-                k_cf_eval<<<nact, 128, 0, st>>>(a.p, b.p, nv, n0.p, cols.p, depth.p, E0d.p, wdev.p, n_w, eta, I.p,
-                                                diff.p);
+                ProfScope ps("cf_eval", st, 0, 40.0 * nact * n_w * double(k - k_eval));
+                k_cf_eval<<<nact, 128, 0, st>>>(a.p, b.p, nv, n0.p, cols.p, k_eval, k, E0d.p, wdev.p, n_w, eta,
+                                                gst.p, Cst.p, Dst.p, I.p, diff.p);
+                k_eval = k;
             }
             ++out.launches;
             MSB_CUDA(cudaMemcpyAsync(hdiff.data(), diff.p, 2 * nv * sizeof(double), cudaMemcpyDeviceToHost, st));
