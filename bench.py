@@ -39,6 +39,7 @@ import workloads  # noqa: E402
 WORKLOADS = {
     "hubbard-L12-fp64": (workloads.CHAIN12, 0, 1e-10, 1e-10),
     "hubbard-L14-mixed": (workloads.CHAIN14, 1, 1e-8, 1e-8),
+    "hubbard-L14-fp64": (workloads.CHAIN14, 0, 1e-10, 1e-10),
     "hubbard-L8-fp64": (workloads.CHAIN8, 0, 1e-10, 1e-10),
     "hubbard-L12x12rhs-mixed": (workloads.BATCH_SITES, 1, 1e-8, 1e-8),
 }

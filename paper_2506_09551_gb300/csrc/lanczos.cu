@@ -781,8 +781,8 @@ __global__ void __launch_bounds__(256, 6) k_cf_apply_hub_f2x2(HubView h0, const 
     }
     const int L = h.L;
     extern __shared__ __align__(16) unsigned char sm_raw[];
-    float2* row = reinterpret_cast<float2*>(sm_raw);                // Ddn values of row u
-    float* lut = reinterpret_cast<float*>(row + h.Ddn);             // 3 (L + 1) diagonal values * sig
+    float2* row = reinterpret_cast<float2*>(sm_raw);                // Ddn values of row u, then two zeros
+    float* lut = reinterpret_cast<float*>(row + h.Ddn + 2);        // 3 (L + 1) diagonal values * sig
     __shared__ int s_uoff[kMaxHops];
     __shared__ float s_usg[kMaxHops];
     __shared__ float red[64];
@@ -800,6 +800,7 @@ __global__ void __launch_bounds__(256, 6) k_cf_apply_hub_f2x2(HubView h0, const 
         const float4* src = reinterpret_cast<const float4*>(Vc + rbase);
         float4* dst = reinterpret_cast<float4*>(row);
         for (int i = threadIdx.x; i < half; i += blockDim.x) dst[i] = src[i];
+        if (threadIdx.x == 0) dst[half] = make_float4(0.f, 0.f, 0.f, 0.f);   // row[Ddn], row[Ddn + 1]
     }
     for (int i = threadIdx.x; i < 3 * (L + 1); i += blockDim.x) {
         const int p = i % (L + 1), nb = i / (L + 1);
@@ -820,7 +821,14 @@ __global__ void __launch_bounds__(256, 6) k_cf_apply_hub_f2x2(HubView h0, const 
     const uint16_t* __restrict__ n16 = reinterpret_cast<const uint16_t*>(h.ndn);
     const uint2* __restrict__ sd2 = reinterpret_cast<const uint2*>(h.sdn);
     float dhi = 0.f, dlo = 0.f;
-    for (int q = threadIdx.x; q < half; q += blockDim.x) {      // elements d0 = 2q, d1 = 2q + 1
+    // Every lane of a warp runs the same iterations (lanes past the row idle, guarded),
+    // so the down-spin loop can use a warp-uniform trip count without divergence.
+    const int iters = (half + blockDim.x - 1) / blockDim.x;
+    const int step = Ddn >> 1;                                  // table slot stride in 32-bit words
+    for (int it = 0; it < iters; ++it) {
+        const int q0 = it * blockDim.x + threadIdx.x;
+        const bool act = q0 < half;
+        const int q = act ? q0 : 0;                             // elements d0 = 2q, d1 = 2q + 1
         float a0x = 0.f, a0y = 0.f, a1x = 0.f, a1y = 0.f;
         int e = 0;
         for (; e + 2 <= nu; e += 2) {
@@ -839,21 +847,15 @@ __global__ void __launch_bounds__(256, 6) k_cf_apply_hub_f2x2(HubView h0, const 
         }
         const uint32_t nn = __ldg(n16 + q);
         const int nd0 = int(nn & 0xFFu), nd1 = int(nn >> 8);
-        const int ndm = nd0 > nd1 ? nd0 : nd1;
-        for (int k = 0; k < ndm; ++k) {
-            const uint32_t tt = __ldg(t32 + (k * Ddn >> 1) + q);
-            if (k < nd0) {
-                const uint32_t h0 = tt & 0xFFFFu;
-                const float2 v = row[h0 >> 1];
-                const float g = (h0 & 1u) ? -1.f : 1.f;
-                a0x = fmaf(g, v.x, a0x); a0y = fmaf(g, v.y, a0y);
-            }
-            if (k < nd1) {
-                const uint32_t h1 = tt >> 16;
-                const float2 v = row[h1 >> 1];
-                const float g = (h1 & 1u) ? -1.f : 1.f;
-                a1x = fmaf(g, v.x, a1x); a1y = fmaf(g, v.y, a1y);
-            }
+        // slots past an element's own count hold the zero slot: no per-hop predicate
+        const int ndw = __reduce_max_sync(0xffffffffu, act ? max(nd0, nd1) : 0);
+        const uint32_t* __restrict__ tp = t32 + q;
+        for (int k = 0; k < ndw; ++k, tp += step) {
+            const uint32_t ta = __ldg(tp);                      // one hop of each element
+            const float2 va = row[(ta & 0xFFFFu) >> 1], vb = row[ta >> 17];
+            const float ga = (ta & 1u) ? -1.f : 1.f, gb = (ta & 0x10000u) ? -1.f : 1.f;
+            a0x = fmaf(ga, va.x, a0x); a0y = fmaf(ga, va.y, a0y);
+            a1x = fmaf(gb, vb.x, a1x); a1y = fmaf(gb, vb.y, a1y);
         }
         const uint2 sd = __ldg(sd2 + q);
         const int nb0 = core >= 0 ? ubits + int((sd.x >> core) & 1u) : 0;
@@ -866,6 +868,7 @@ __global__ void __launch_bounds__(256, 6) k_cf_apply_hub_f2x2(HubView h0, const 
         wv.y = fmaf(mt, a0y, dg0 * x0.y);
         wv.z = fmaf(mt, a1x, dg1 * x1.x);
         wv.w = fmaf(mt, a1y, dg1 * x1.y);
+        if (!act) continue;                                      // warp-uniform part done
         if (has_prev) {
             const float4 y = __ldcs(Pc4 + (rbase >> 1) + q);
             wv.x = fmaf(mcB, y.x, wv.x);
@@ -1094,7 +1097,7 @@ static void cf_impl(const CFColumns& P, const View& view, const double* w, int n
             pair = pair && h.Ddn % 2 == 0 && h.hdn16 != nullptr;
             fx = fx && h.hdn16 != nullptr;
         }
-        hub_smem = maxDdn * int64_t(sizeof(C)) + 3 * (maxL + 1) * 8;
+        hub_smem = (maxDdn + 2) * int64_t(sizeof(C)) + 3 * (maxL + 1) * 8;   // row, two zero slots, table
         rows = rows && hub_smem <= 160 * 1024;
         if (rows) {
             nblkA = int(maxDup);

@@ -32,7 +32,9 @@ static void build_hubbard(msb_op* op, const msb_model& m, int intermediate) {
     op->sdn.alloc(op->host_dn.size()); op->sdn.upload(op->host_dn.data(), op->host_dn.size());
     if (op->host_dn.size() < 32768) {
         std::vector<uint16_t> t16(td.size());
-        for (size_t i = 0; i < td.size(); ++i) t16[i] = td[i] < 0 ? uint16_t(0xFFFF) : uint16_t(td[i]);
+        // empty slots point at index Ddn, where the row-tiled FP32 apply keeps a zero
+        const uint16_t empty = uint16_t(op->host_dn.size() << 1);
+        for (size_t i = 0; i < td.size(); ++i) t16[i] = td[i] < 0 ? empty : uint16_t(td[i]);
         op->hdn16.alloc(t16.size());
         op->hdn16.upload(t16.data(), t16.size());
     }

@@ -63,7 +63,8 @@ struct HubView {
     const int32_t* hdn;
     const uint8_t* nup;
     const uint8_t* ndn;
-    const uint16_t* hdn16;  // [slot][state] down-spin table with 16-bit entries (Ddn < 32768), else null
+    const uint16_t* hdn16;  // [slot][state] down-spin table with 16-bit entries (Ddn < 32768), else null;
+                            // empty slots hold Ddn << 1 (index Ddn: a zero kept past the staged row)
     const uint32_t* sup;   // occupation strings, rank order
     const uint32_t* sdn;
     double t, U, Uc;
