@@ -659,7 +659,7 @@ __global__ void __launch_bounds__(256, 5) k_cf_apply_hub_fx(HubView h0, const Hu
     const int L = h.L;
     extern __shared__ __align__(16) unsigned char sm_raw[];
     longlong2* row = reinterpret_cast<longlong2*>(sm_raw);          // row u of V_k in fixed point
-    double* lut = reinterpret_cast<double*>(row + h.Ddn);           // 3 (L + 1) diagonal values * sig
+    double* lut = reinterpret_cast<double*>(row + h.Ddn + 2);       // 3 (L + 1) diagonal values * sig
     __shared__ int s_uoff[kMaxHops];
     __shared__ int s_uneg[kMaxHops];
     __shared__ double red[32];
@@ -678,6 +678,7 @@ __global__ void __launch_bounds__(256, 5) k_cf_apply_hub_fx(HubView h0, const Hu
         const double2 v = Vc[rbase + d];
         row[d] = make_longlong2(fx_term(v.x, eB, 0), fx_term(v.y, eB, 0));
     }
+    if (threadIdx.x == 0) row[Ddn] = make_longlong2(0, 0);        // target of the empty down-spin slots
     for (int i = threadIdx.x; i < 3 * (L + 1); i += blockDim.x) {
         const int p = i % (L + 1), nb = i / (L + 1);
         lut[i] = sig * (h.U * double(p) - h.Uc * double(nb));
@@ -695,7 +696,13 @@ __global__ void __launch_bounds__(256, 5) k_cf_apply_hub_fx(HubView h0, const Hu
     const double mcB = -cB;
     const uint16_t* __restrict__ t16 = h.hdn16;                     // [slot][state], (target << 1) | neg
     double dot = 0.0;
-    for (int d = threadIdx.x; d < Ddn; d += blockDim.x) {
+    // Every lane of a warp runs the same iterations (lanes past the row idle,
+    // guarded), so the down-spin loop runs to a warp-uniform count.
+    const int iters = (Ddn + blockDim.x - 1) / blockDim.x;
+    for (int it = 0; it < iters; ++it) {
+        const int d0 = it * blockDim.x + threadIdx.x;
+        const bool act = d0 < Ddn;
+        const int d = act ? d0 : 0;
         long long ax = 0, ay = 0;
         int e = 0;
         for (; e + 4 <= nu; e += 4) {
@@ -717,7 +724,8 @@ __global__ void __launch_bounds__(256, 5) k_cf_apply_hub_fx(HubView h0, const Hu
             ax += fx_term(v.x, eB, g);
             ay += fx_term(v.y, eB, g);
         }
-        const int nd = __ldg(h.ndn + d);
+        // slots past an element's own count hold the zero slot: no per-hop predicate
+        const int nd = __reduce_max_sync(0xffffffffu, act ? int(__ldg(h.ndn + d)) : 0);
         e = 0;
         for (; e + 4 <= nd; e += 4) {
             const int h0 = __ldg(t16 + e * Ddn + d), h1 = __ldg(t16 + (e + 1) * Ddn + d);
@@ -743,6 +751,7 @@ __global__ void __launch_bounds__(256, 5) k_cf_apply_hub_fx(HubView h0, const Hu
         const uint32_t sd = __ldg(h.sdn + d);
         const int nb = core >= 0 ? ubits + int((sd >> core) & 1u) : 0;
         const double dg = lut[__popc(su & sd) + nb * (L + 1)];
+        if (!act) continue;                                      // warp-uniform part done
         const double2 x = Vc[rbase + d];
         double2 wv;
         wv.x = fma(mts, __ll2double_rn(ax), dg * x.x);
