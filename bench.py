@@ -202,6 +202,31 @@ def run_cpu_baseline(name: str) -> dict:
 
 
 # ---------------------------------------------------------------------------
+# Multi-rank logic: independent problems per rank, no collective on the data path
+# ---------------------------------------------------------------------------
+def max_over_ranks(x: float, world: int) -> float:
+    """The largest x over all ranks (the whole job's time is the slowest rank's)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def rank_core_site(rank: int, L: int) -> int:
+    """The core-hole site whose map this rank computes (translation-equivalent problems)."""
+    return rank % L
+
+
+def job_throughput(units_per_rank: float, world: int, seconds: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return world * units_per_rank / seconds
+
+
+# ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
 def measured_traffic(workload, kernel, alg_bytes_per_launch):
@@ -280,12 +305,7 @@ def gpu_arm_csr(args, rank, world):
         e1.synchronize()
     lib.msb_profile_enable(0)
     stats = native.profile_read()
-    ms = e0.elapsed_time(e1) / args.steps
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world)
     # end to end: host matrix and right-hand side in, host solutions out
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -297,19 +317,19 @@ def gpu_arm_csr(args, rank, world):
         xh = x2.cpu()
         del op2, x2, xh
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
     top, roof = dominant_roofline(stats, prec, measured_peaks())
     total_ms = sum(s_["ms"] for s_ in stats)
     csz = 16 if prec == 0 else 8
     return {
         "metric": "shifted solves/s (random complex-symmetric CSR)",
-        "value": world * wl.n_shifts / (ms * 1e-3),
+        "value": job_throughput(wl.n_shifts, world, ms * 1e-3),
         "unit": "solves/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "c128" if prec == 0 else "c64 vectors, f64 scalars", "data": "synthetic random CSR",
         "config": {"workload": args.workload, "n": wl.n, "nnz": int(len(val)), "n_shifts": wl.n_shifts,
                    "tol": tol, "seed_shift": seed, "l2": "working set larger than L2; no flush needed"},
-        "e2e": {"value": world * wl.n_shifts / e2e_s, "unit": "solves/s",
+        "e2e": {"value": job_throughput(wl.n_shifts, world, e2e_s), "unit": "solves/s",
                 "h2d_bytes_per_step": int(rowptr.nbytes + col.nbytes + val.nbytes + wl.n * 16),
                 "d2h_bytes_per_step": int(wl.n_shifts * wl.n * csz), "seconds": e2e_s},
         "gpu_launches": int(info["kernel_launches"]),
@@ -333,10 +353,11 @@ def gpu_arm(args, rank, world):
     if args.workload in CLUSTERS:
         clusters, prec, stol, ctol = CLUSTERS[args.workload]
         wl = clusters[-1]
-        models = [api.model(c.L, c.n_up, c.n_dn, c.t, c.U, c.Uc, core_site=rank % c.L) for c in clusters]
+        models = [api.model(c.L, c.n_up, c.n_dn, c.t, c.U, c.Uc, core_site=rank_core_site(rank, c.L))
+                  for c in clusters]
     else:
         wl, prec, stol, ctol = WORKLOADS[args.workload]
-    core = rank % wl.L
+    core = rank_core_site(rank, wl.L)
     m = api.model(wl.L, wl.n_up, wl.n_dn, wl.t, wl.U, wl.Uc, core_site=core)
     p = api.map_params(Gamma=wl.Gamma, eta=wl.eta, gs_tol=wl.gs_tol, solve_tol=stol, cf_tol=ctol, precision=prec)
     H = api.Operator.hubbard(m, False)
@@ -392,15 +413,10 @@ def gpu_arm(args, rank, world):
     stats = native.profile_read()
     ms = e0.elapsed_time(e1) / args.steps
     clocks = clk.summary()
-    # whole-job time = max over ranks
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world)          # whole-job time = the slowest rank's
     n_maps = len(clusters) if clusters else (len(sites) if sites else 1)
     pts = len(w_in) * len(w) * n_maps
-    value = world * pts / (ms * 1e-3)
+    value = job_throughput(pts, world, ms * 1e-3)
 
     print(f"[bench] {args.workload}: {ms:.1f} ms per map over {args.steps} steps", file=sys.stderr, flush=True)
     # end to end through the public host API (operators built, grids in, map out)
@@ -415,12 +431,7 @@ def gpu_arm(args, rank, world):
     else:
         I_host, info_e2e, _ = api.rixs_map(m, p, w_in, w)
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
     I_dev = out.cpu().numpy()
     same = (float(np.max(np.abs(I_dev - I_host)) / np.max(np.abs(I_host)))
             if I_host is not None and np.max(np.abs(I_host)) > 0 else None)
@@ -452,7 +463,7 @@ def gpu_arm(args, rank, world):
                    "parallelism": f"{world} independent maps (core site = rank)",
                    "l2": "working set (vectors of GBs) larger than L2; no flush needed"},
         "e2e": None if args.no_e2e else {
-            "value": world * pts / e2e_s, "unit": "map points/s",
+            "value": job_throughput(pts, world, e2e_s), "unit": "map points/s",
             "h2d_bytes_per_step": int(8 * (len(w_in) + len(w))) + 2 * 8 * 4,
             "d2h_bytes_per_step": int(8 * pts), "seconds": e2e_s,
             "max_rel_diff_vs_value_map": same},
