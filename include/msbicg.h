@@ -143,6 +143,20 @@ msb_status msb_basis_states(const msb_basis *b, int species, uint32_t *out);
 
 void msb_basis_destroy(msb_basis *b);
 
+/* Shared-memory placement of a down-spin row used by the FP32 continued-fraction
+ * apply.  That kernel stages each row of a vector in shared memory and gathers
+ * the down-spin hop targets from it; since the hop table is the same for every
+ * row, the library places element d at a slot chosen once per sector, so that
+ * the gathers of a half-warp hit fewer shared-memory bank conflicts (a
+ * deterministic hill climb; no effect on any result).  Host only, no device.
+ * slot: HOST array of D_dn entries (may be NULL): slot[d] for each down state
+ * d (a permutation of 0..D_dn-1).  cost_plain / cost_layout (may be NULL): the
+ * mean worst-bank count per half-warp gather for slot[d] = d and for the
+ * chosen slots (1 is conflict free).  Errors: MSB_EINVAL if D_dn is odd or
+ * not below 32768, or periodic with L < 3. */
+msb_status msb_basis_row_layout(const msb_basis *b, int periodic, uint16_t *slot, double *cost_plain,
+                                double *cost_layout);
+
 /* ------------------------------------------------------------------------ */
 /* Operators A = H, H' (matrix-free) or a user CSR matrix                    */
 /* ------------------------------------------------------------------------ */

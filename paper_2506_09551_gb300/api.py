@@ -63,6 +63,24 @@ def basis_states(L: int, n_up: int, n_dn: int):
         lib.msb_basis_destroy(h)
 
 
+def row_layout(L: int, n_dn: int, periodic: bool = True):
+    """Shared-memory slot of each down-spin state used by the FP32 continued-fraction
+    apply, and the mean worst-bank count per half-warp gather without / with it."""
+    lib = N.load()
+    h = C.c_void_p()
+    N.check(lib.msb_basis_create(L, 0, n_dn, C.byref(h)))
+    try:
+        dd = C.c_int64()
+        N.check(lib.msb_basis_dims(h, None, C.byref(dd), None))
+        slot = np.zeros(dd.value, dtype=np.uint16)
+        c0, c1 = C.c_double(), C.c_double()
+        N.check(lib.msb_basis_row_layout(h, 1 if periodic else 0, slot.ctypes.data_as(C.POINTER(C.c_uint16)),
+                                         C.byref(c0), C.byref(c1)))
+        return slot, c0.value, c1.value
+    finally:
+        lib.msb_basis_destroy(h)
+
+
 class Operator:
     """Handle of a library operator (matrix-free Hubbard H / H', or CSR)."""
 

@@ -9,6 +9,9 @@
 // orbitals because they are passed twice (once by c, once by c^dag).
 #include <algorithm>
 #include <cstring>
+#include <tuple>
+#include <mutex>
+#include <map>
 
 #include "kernels.cuh"
 
@@ -50,6 +53,152 @@ void hop_table(int L, int n, bool periodic, const std::vector<uint32_t>& states,
         }
         count[k] = uint8_t(c);
     }
+}
+
+// ---------------------------------------------------------------------------
+// Shared-memory placement of a down-spin row for the FP32 row-tiled apply.
+//
+// The apply stages row u of V_k in shared memory and gathers the down-spin hop
+// targets from it: lane l of warp w handles elements 2q, 2q+1 with
+// q = it * threads + 32 w + l, and at hop slot k every lane loads one 8-byte word
+// per element (the zero slot at index D once the element's own hops are done;
+// the trip count is the warp's largest hop count).  A 32-lane 8-byte load is
+// served per half-warp, and two different words on one bank pair (32 banks of
+// 4 bytes) serialise.  The hop table is the same for every row u, so the slot of
+// each element can be chosen once per sector: a hill climb over swaps of two
+// elements on different bank pairs lowers the summed worst-bank count of all
+// the access sets.  Deterministic (fixed seed).
+// ---------------------------------------------------------------------------
+RowLayout row_layout(const std::vector<int32_t>& table, const std::vector<uint8_t>& count, int64_t D, int W,
+                     int threads) {
+    MSB_REQUIRE(D >= 2 && D % 2 == 0 && D < 32768, "row layout needs an even D < 32768");
+    MSB_REQUIRE(threads >= 32 && threads % 32 == 0, "threads must be a multiple of 32");
+    const int64_t half = D / 2;
+    const int32_t ZERO = int32_t(D);
+    // access sets: one per (half-warp, slot, parity), unique members
+    std::vector<int32_t> mem;              // concatenated members
+    std::vector<int64_t> beg{0};
+    std::vector<int32_t> tmp;
+    const int64_t iters = (half + threads - 1) / threads;
+    for (int64_t it = 0; it < iters; ++it)
+        for (int w = 0; w < threads / 32; ++w) {
+            const int64_t q0 = it * threads + int64_t(w) * 32;
+            if (q0 >= half) continue;
+            int ndw = 0;
+            for (int l = 0; l < 32 && q0 + l < half; ++l)
+                ndw = std::max(ndw, int(std::max(count[2 * (q0 + l)], count[2 * (q0 + l) + 1])));
+            for (int hw = 0; hw < 2; ++hw)
+                for (int k = 0; k < ndw; ++k)
+                    for (int par = 0; par < 2; ++par) {
+                        tmp.clear();
+                        for (int l = 0; l < 16; ++l) {
+                            const int64_t q = q0 + hw * 16 + l;
+                            if (q >= half) break;
+                            const int64_t d = 2 * q + par;
+                            tmp.push_back(k < count[d] ? (table[size_t(k) * D + d] >> 1) : ZERO);
+                        }
+                        if (tmp.empty()) continue;
+                        std::sort(tmp.begin(), tmp.end());
+                        tmp.erase(std::unique(tmp.begin(), tmp.end()), tmp.end());
+                        mem.insert(mem.end(), tmp.begin(), tmp.end());
+                        beg.push_back(int64_t(mem.size()));
+                    }
+        }
+    (void)W;
+    const int64_t nsets = int64_t(beg.size()) - 1;
+    std::vector<std::vector<int32_t>> sets_of(static_cast<size_t>(D));
+    for (int64_t si = 0; si < nsets; ++si)
+        for (int64_t j = beg[si]; j < beg[si + 1]; ++j)
+            if (mem[j] != ZERO) sets_of[mem[j]].push_back(int32_t(si));
+    std::vector<int32_t> pos(size_t(D) + 1);
+    for (int64_t e = 0; e <= D; ++e) pos[e] = int32_t(e);
+    std::vector<uint8_t> cnt(size_t(nsets) * 16, 0);
+    std::vector<uint8_t> cur(size_t(nsets), 0);
+    auto setmax = [&](int64_t si) {
+        uint8_t m = 0;
+        for (int b = 0; b < 16; ++b) m = std::max(m, cnt[size_t(si) * 16 + b]);
+        return m;
+    };
+    double plain = 0;
+    for (int64_t si = 0; si < nsets; ++si) {
+        for (int64_t j = beg[si]; j < beg[si + 1]; ++j) ++cnt[size_t(si) * 16 + (pos[mem[j]] & 15)];
+        cur[si] = setmax(si);
+        plain += cur[si];
+    }
+    double total = plain;
+    std::vector<int64_t> stamp(size_t(nsets), -1);
+    uint64_t rs = 0x9E3779B97F4A7C15ull;
+    auto rnd = [&]() {                         // splitmix64
+        uint64_t z = (rs += 0x9E3779B97F4A7C15ull);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return z ^ (z >> 31);
+    };
+    std::vector<int32_t> touched;
+    const int64_t trials = 300 * D;
+    for (int64_t t = 0; t < trials; ++t) {
+        const int32_t x = int32_t(rnd() % uint64_t(D)), y = int32_t(rnd() % uint64_t(D));
+        const int bx = pos[x] & 15, by = pos[y] & 15;
+        if (bx == by) continue;
+        for (int32_t si : sets_of[x]) stamp[si] = 2 * t;          // sets of x
+        touched.clear();
+        long delta = 0;
+        for (int32_t si : sets_of[y]) {
+            if (stamp[si] == 2 * t) { stamp[si] = 2 * t + 1; continue; }   // holds both: unchanged
+            uint8_t* c = &cnt[size_t(si) * 16];
+            --c[by]; ++c[bx];
+            touched.push_back(si);
+        }
+        for (int32_t si : sets_of[x]) {
+            if (stamp[si] != 2 * t) continue;
+            uint8_t* c = &cnt[size_t(si) * 16];
+            --c[bx]; ++c[by];
+            touched.push_back(si);
+        }
+        for (int32_t si : touched) delta += long(setmax(si)) - long(cur[si]);
+        if (delta <= 0) {
+            for (int32_t si : touched) cur[si] = setmax(si);
+            std::swap(pos[x], pos[y]);
+            total += double(delta);
+        } else {                                                // undo
+            for (int32_t si : sets_of[y]) {
+                if (stamp[si] == 2 * t + 1) continue;
+                uint8_t* c = &cnt[size_t(si) * 16];
+                ++c[by]; --c[bx];
+            }
+            for (int32_t si : sets_of[x]) {
+                if (stamp[si] != 2 * t) continue;
+                uint8_t* c = &cnt[size_t(si) * 16];
+                ++c[bx]; --c[by];
+            }
+        }
+    }
+    RowLayout out;
+    out.perm.resize(size_t(D));
+    std::vector<uint8_t> seen(size_t(D), 0);
+    for (int64_t e = 0; e < D; ++e) {
+        MSB_REQUIRE(pos[e] >= 0 && pos[e] < D && !seen[pos[e]], "row layout is not a permutation");
+        seen[pos[e]] = 1;
+        out.perm[e] = uint16_t(pos[e]);
+    }
+    out.cost_plain = nsets ? plain / double(nsets) : 0.0;
+    out.cost_layout = nsets ? total / double(nsets) : 0.0;
+    return out;
+}
+
+const RowLayout& cached_row_layout(int L, int n, bool periodic, int threads) {
+    static std::mutex mu;
+    static std::map<std::tuple<int, int, bool, int>, RowLayout> cache;
+    std::lock_guard<std::mutex> lock(mu);
+    const auto key = std::make_tuple(L, n, periodic, threads);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    const auto states = sector_states(L, n);
+    std::vector<int32_t> table;
+    std::vector<uint8_t> count;
+    int W = 0;
+    hop_table(L, n, periodic, states, table, count, W);
+    return cache.emplace(key, row_layout(table, count, int64_t(states.size()), W, threads)).first->second;
 }
 
 void validate_model(const msb_model& m) {
@@ -95,3 +244,17 @@ extern "C" msb_status msb_basis_states(const msb_basis* b, int species, uint32_t
 }
 
 extern "C" void msb_basis_destroy(msb_basis* b) { delete b; }
+
+extern "C" msb_status msb_basis_row_layout(const msb_basis* b, int periodic, uint16_t* slot, double* cost_plain,
+                                           double* cost_layout) {
+    return msb::guard("msb_basis_row_layout", [&] {
+        MSB_REQUIRE(b != nullptr, "basis is NULL");
+        const int64_t D = int64_t(b->dn.size());
+        MSB_REQUIRE(D >= 2 && D % 2 == 0 && D < 32768, "the row layout needs an even D_dn below 32768");
+        MSB_REQUIRE(!(periodic && b->L < 3), "a periodic chain needs L >= 3");
+        const auto& lay = msb::cached_row_layout(b->L, b->n_dn, periodic != 0, msb::kApplyThreads);
+        if (slot) std::memcpy(slot, lay.perm.data(), lay.perm.size() * sizeof(uint16_t));
+        if (cost_plain) *cost_plain = lay.cost_plain;
+        if (cost_layout) *cost_layout = lay.cost_layout;
+    });
+}

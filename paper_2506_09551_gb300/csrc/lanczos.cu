@@ -805,11 +805,25 @@ __global__ void __launch_bounds__(256, 6) k_cf_apply_hub_f2x2(HubView h0, const 
     const bool has_prev = cB != 0.f;
     const uint32_t su = __ldg(h.sup + u);
     const int nu = __ldg(h.nup + u);
+    // Row u into shared memory: element d at slot16[d] when the sector has a
+    // bank-aware placement (fewer conflicts in the random down-spin gathers),
+    // else at d.
+    const bool placed = h.slot16 != nullptr;
     {
         const float4* src = reinterpret_cast<const float4*>(Vc + rbase);
-        float4* dst = reinterpret_cast<float4*>(row);
-        for (int i = threadIdx.x; i < half; i += blockDim.x) dst[i] = src[i];
-        if (threadIdx.x == 0) dst[half] = make_float4(0.f, 0.f, 0.f, 0.f);   // row[Ddn], row[Ddn + 1]
+        if (placed) {
+            const uint32_t* sl2 = reinterpret_cast<const uint32_t*>(h.slot16);   // slots of 2i, 2i + 1
+            for (int i = threadIdx.x; i < half; i += blockDim.x) {
+                const float4 v = src[i];
+                const uint32_t sp = __ldg(sl2 + i);
+                row[sp & 0xFFFFu] = make_float2(v.x, v.y);
+                row[sp >> 16] = make_float2(v.z, v.w);
+            }
+        } else {
+            float4* dst = reinterpret_cast<float4*>(row);
+            for (int i = threadIdx.x; i < half; i += blockDim.x) dst[i] = src[i];
+        }
+        if (threadIdx.x == 0) reinterpret_cast<float4*>(row)[half] = make_float4(0.f, 0.f, 0.f, 0.f);   // row[Ddn], row[Ddn + 1]
     }
     for (int i = threadIdx.x; i < 3 * (L + 1); i += blockDim.x) {
         const int p = i % (L + 1), nb = i / (L + 1);
@@ -826,7 +840,7 @@ __global__ void __launch_bounds__(256, 6) k_cf_apply_hub_f2x2(HubView h0, const 
     const float mt = -h.tf * sig;
     const float mcB = -cB;
     const float4* __restrict__ Vc4 = reinterpret_cast<const float4*>(Vc);
-    const uint32_t* __restrict__ t32 = reinterpret_cast<const uint32_t*>(h.hdn16);
+    const uint32_t* __restrict__ t32 = reinterpret_cast<const uint32_t*>(placed ? h.hdn16p : h.hdn16);
     const uint16_t* __restrict__ n16 = reinterpret_cast<const uint16_t*>(h.ndn);
     const uint2* __restrict__ sd2 = reinterpret_cast<const uint2*>(h.sdn);
     float dhi = 0.f, dlo = 0.f;
@@ -871,7 +885,15 @@ __global__ void __launch_bounds__(256, 6) k_cf_apply_hub_f2x2(HubView h0, const 
         const int nb1 = core >= 0 ? ubits + int((sd.y >> core) & 1u) : 0;
         const float dg0 = lut[__popc(su & sd.x) + nb0 * (L + 1)];
         const float dg1 = lut[__popc(su & sd.y) + nb1 * (L + 1)];
-        const float2 x0 = row[2 * q], x1 = row[2 * q + 1];
+        float2 x0, x1;
+        if (placed) {                                           // own values: from global (L1/L2)
+            const float4 xv = Vc4[(rbase >> 1) + q];
+            x0 = make_float2(xv.x, xv.y);
+            x1 = make_float2(xv.z, xv.w);
+        } else {
+            x0 = row[2 * q];
+            x1 = row[2 * q + 1];
+        }
         float4 wv;
         wv.x = fmaf(mt, a0x, dg0 * x0.x);
         wv.y = fmaf(mt, a0y, dg0 * x0.y);
@@ -1184,10 +1206,10 @@ static void cf_impl(const CFColumns& P, const View& view, const double* w, int n
                     auto xm = reinterpret_cast<const double2*>(vkm1);
                     auto y = reinterpret_cast<double2*>(wv);
                     if (multi)
-                        k_cf_apply_hub_fx<true><<<g, 256, hub_smem, st>>>(view, hv.p, colq.p, x, xm, y, ld, cols.p,
+                        k_cf_apply_hub_fx<true><<<g, kApplyThreads, hub_smem, st>>>(view, hv.p, colq.p, x, xm, y, ld, cols.p,
                                                                           cf, part.p);
                     else
-                        k_cf_apply_hub_fx<false><<<g, 256, hub_smem, st>>>(view, hv.p, colq.p, x, xm, y, ld,
+                        k_cf_apply_hub_fx<false><<<g, kApplyThreads, hub_smem, st>>>(view, hv.p, colq.p, x, xm, y, ld,
                                                                            cols.p, cf, part.p);
                     done_hub = true;
                 } else if (rows && pair) {
@@ -1195,18 +1217,18 @@ static void cf_impl(const CFColumns& P, const View& view, const double* w, int n
                     auto xm = reinterpret_cast<const float2*>(vkm1);
                     auto y = reinterpret_cast<float2*>(wv);
                     if (multi)
-                        k_cf_apply_hub_f2x2<true><<<g, 256, hub_smem, st>>>(view, hv.p, colq.p, x, xm, y, ld,
+                        k_cf_apply_hub_f2x2<true><<<g, kApplyThreads, hub_smem, st>>>(view, hv.p, colq.p, x, xm, y, ld,
                                                                             cols.p, cf, part.p);
                     else
-                        k_cf_apply_hub_f2x2<false><<<g, 256, hub_smem, st>>>(view, hv.p, colq.p, x, xm, y, ld,
+                        k_cf_apply_hub_f2x2<false><<<g, kApplyThreads, hub_smem, st>>>(view, hv.p, colq.p, x, xm, y, ld,
                                                                              cols.p, cf, part.p);
                     done_hub = true;
                 } else if (rows) {
                     if (multi)
-                        k_cf_apply_hub<C, true><<<g, 256, hub_smem, st>>>(view, hv.p, colq.p, vk, vkm1, wv, ld,
+                        k_cf_apply_hub<C, true><<<g, kApplyThreads, hub_smem, st>>>(view, hv.p, colq.p, vk, vkm1, wv, ld,
                                                                           cols.p, cf, part.p);
                     else
-                        k_cf_apply_hub<C, false><<<g, 256, hub_smem, st>>>(view, hv.p, colq.p, vk, vkm1, wv, ld,
+                        k_cf_apply_hub<C, false><<<g, kApplyThreads, hub_smem, st>>>(view, hv.p, colq.p, vk, vkm1, wv, ld,
                                                                            cols.p, cf, part.p);
                     done_hub = true;
                 }

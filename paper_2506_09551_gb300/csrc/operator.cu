@@ -37,6 +37,24 @@ static void build_hubbard(msb_op* op, const msb_model& m, int intermediate) {
         for (size_t i = 0; i < td.size(); ++i) t16[i] = td[i] < 0 ? empty : uint16_t(td[i]);
         op->hdn16.alloc(t16.size());
         op->hdn16.upload(t16.data(), t16.size());
+        if (op->host_dn.size() % 2 == 0 && op->host_dn.size() >= 2) {
+            // targets moved to their shared-memory slots for the FP32 row-tiled apply
+            const int64_t D = int64_t(op->host_dn.size());
+            const RowLayout& lay = cached_row_layout(m.L, op->sec_dn, m.periodic != 0, kApplyThreads);
+            MSB_REQUIRE(int64_t(lay.perm.size()) == D, "row layout size mismatch");
+            std::vector<uint16_t> tp(td.size());
+            for (size_t i = 0; i < td.size(); ++i) {
+                if (td[i] < 0) { tp[i] = empty; continue; }
+                const int32_t t = td[i] >> 1;
+                MSB_REQUIRE(t >= 0 && t < D, "hop target out of range");
+                tp[i] = uint16_t((int32_t(lay.perm[t]) << 1) | (td[i] & 1));
+            }
+            for (uint16_t v : tp) MSB_REQUIRE((v >> 1) <= D, "permuted hop entry out of range");
+            op->hdn16p.alloc(tp.size());
+            op->hdn16p.upload(tp.data(), tp.size());
+            op->slot16.alloc(lay.perm.size());
+            op->slot16.upload(lay.perm.data(), lay.perm.size());
+        }
     }
     MSB_CUDA(cudaDeviceSynchronize());
     HubView& h = op->hub;
@@ -47,6 +65,8 @@ static void build_hubbard(msb_op* op, const msb_model& m, int intermediate) {
     h.hup = op->hup.p; h.hdn = op->hdn.p;
     h.nup = op->nup.p; h.ndn = op->ndn.p;
     h.hdn16 = op->hdn16.p;
+    h.hdn16p = op->hdn16p.p;
+    h.slot16 = op->slot16.p;
     h.sup = op->sup.p; h.sdn = op->sdn.p;
     h.t = m.t; h.U = m.U; h.Uc = m.Uc;
     h.tf = float(m.t); h.Uf = float(m.U); h.Ucf = float(m.Uc);

@@ -65,6 +65,8 @@ struct HubView {
     const uint8_t* ndn;
     const uint16_t* hdn16;  // [slot][state] down-spin table with 16-bit entries (Ddn < 32768), else null;
                             // empty slots hold Ddn << 1 (index Ddn: a zero kept past the staged row)
+    const uint16_t* hdn16p; // the same with targets moved to their shared-memory slots (FP32 apply), or null
+    const uint16_t* slot16; // shared-memory slot of each down-spin state (with hdn16p), or null
     const uint32_t* sup;   // occupation strings, rank order
     const uint32_t* sdn;
     double t, U, Uc;
@@ -183,7 +185,7 @@ struct msb_op {
     int sec_up = 0, sec_dn = 0;  // electrons of this operator's sector
     msb::DevBuf<int32_t> hup, hdn;
     msb::DevBuf<uint8_t> nup, ndn;
-    msb::DevBuf<uint16_t> hdn16;
+    msb::DevBuf<uint16_t> hdn16, hdn16p, slot16;
     msb::DevBuf<uint32_t> sup, sdn;
     std::vector<uint32_t> host_up, host_dn;
     msb::HubView hub{};
@@ -210,6 +212,18 @@ struct msb_op {
 };
 
 namespace msb {
+// Threads per CTA of the row-tiled continued-fraction apply kernels.
+constexpr int kApplyThreads = 256;
+// Shared-memory slot of each down-spin element for the FP32 row-tiled apply
+// (basis.cu): perm[d] = slot of element d; costs = mean worst-bank count per
+// half-warp gather, plain layout and chosen layout.
+struct RowLayout {
+    std::vector<uint16_t> perm;
+    double cost_plain = 0, cost_layout = 0;
+};
+RowLayout row_layout(const std::vector<int32_t>& table, const std::vector<uint8_t>& count, int64_t D, int W,
+                     int threads);
+const RowLayout& cached_row_layout(int L, int n, bool periodic, int threads);
 // Host-side sector enumeration and hopping tables (basis.cu).
 std::vector<uint32_t> sector_states(int L, int n);
 // ELL hop table [W][D] with entries (target << 1) | neg, -1 empty; counts per state.

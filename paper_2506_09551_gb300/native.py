@@ -67,6 +67,7 @@ SIGNATURES = {
     "msb_basis_states": (_I, [_P, _I, C.POINTER(C.c_uint32)]),
     "msb_basis_destroy": (None, [_P]),
     "msb_op_create_hubbard": (_I, [C.POINTER(msb_model), _I, C.POINTER(_P)]),
+    "msb_basis_row_layout": (_I, [_P, _I, C.POINTER(C.c_uint16), _PD, _PD]),
     "msb_op_create_csr": (_I, [_I64, C.POINTER(C.c_int64), C.POINTER(C.c_int32), _PD, C.POINTER(_P)]),
     "msb_op_create_direct_sum": (_I, [C.POINTER(_P), _PD, _I, C.POINTER(_P)]),
     "msb_op_dim": (_I, [_P, C.POINTER(_I64)]),
