@@ -1130,6 +1130,7 @@ static void cf_impl(const CFColumns& P, const View& view, const double* w, int n
         }
         hub_smem = (maxDdn + 2) * int64_t(sizeof(C)) + 3 * (maxL + 1) * 8;   // row, two zero slots, table
         rows = rows && hub_smem <= 160 * 1024;
+        if (std::is_same<C, double2>::value && !fx) rows = false;   // FP64 rows need the 16-bit table
         if (rows) {
             nblkA = int(maxDup);
             const void* fn = nullptr;
@@ -1138,7 +1139,7 @@ static void cf_impl(const CFColumns& P, const View& view, const double* w, int n
             else if (pair)
                 fn = multi ? (const void*)k_cf_apply_hub_f2x2<true> : (const void*)k_cf_apply_hub_f2x2<false>;
             else
-                fn = multi ? (const void*)k_cf_apply_hub<C, true> : (const void*)k_cf_apply_hub<C, false>;
+                fn = multi ? (const void*)k_cf_apply_hub<float2, true> : (const void*)k_cf_apply_hub<float2, false>;
             MSB_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(hub_smem)));
         }
     }
@@ -1224,13 +1225,16 @@ static void cf_impl(const CFColumns& P, const View& view, const double* w, int n
                                                                              cols.p, cf, part.p);
                     done_hub = true;
                 } else if (rows) {
-                    if (multi)
-                        k_cf_apply_hub<C, true><<<g, kApplyThreads, hub_smem, st>>>(view, hv.p, colq.p, vk, vkm1, wv, ld,
-                                                                          cols.p, cf, part.p);
-                    else
-                        k_cf_apply_hub<C, false><<<g, kApplyThreads, hub_smem, st>>>(view, hv.p, colq.p, vk, vkm1, wv, ld,
-                                                                           cols.p, cf, part.p);
-                    done_hub = true;
+                    // FP32 with an odd D_dn (FP64 always takes the fixed-point kernel)
+                    if constexpr (std::is_same<C, float2>::value) {
+                        if (multi)
+                            k_cf_apply_hub<C, true><<<g, kApplyThreads, hub_smem, st>>>(view, hv.p, colq.p, vk, vkm1,
+                                                                                        wv, ld, cols.p, cf, part.p);
+                        else
+                            k_cf_apply_hub<C, false><<<g, kApplyThreads, hub_smem, st>>>(view, hv.p, colq.p, vk, vkm1,
+                                                                                         wv, ld, cols.p, cf, part.p);
+                        done_hub = true;
+                    }
                 }
             }
             if (!done_hub)
