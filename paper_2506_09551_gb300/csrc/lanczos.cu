@@ -641,6 +641,7 @@ __device__ __forceinline__ long long fx_term(double v, int eB, long long neg) {
 
 __device__ __forceinline__ long long fx_signed(long long f, long long neg) { return (f ^ neg) - neg; }
 
+
 template <bool Multi>
 __global__ void __launch_bounds__(256, 5) k_cf_apply_hub_fx(HubView h0, const HubView* __restrict__ hv,
                                                             const int* __restrict__ colq,
@@ -1110,6 +1111,7 @@ static void cf_impl(const CFColumns& P, const View& view, const double* w, int n
     const int grid = grid_for(ld / per, 256, 4);
     int64_t hub_smem = 0;
     bool rows = false, pair = false, fx = false;
+    int fx_threads = 256;
     int nblkA = grid;
     std::vector<HubView> hviews;
     if constexpr (hub) {
@@ -1130,6 +1132,11 @@ static void cf_impl(const CFColumns& P, const View& view, const double* w, int n
         }
         hub_smem = (maxDdn + 2) * int64_t(sizeof(C)) + 3 * (maxL + 1) * 8;   // row, two zero slots, table
         rows = rows && hub_smem <= 160 * 1024;
+        // FP64 fixed-point kernel: rows of up to 1024 elements take 128-thread CTAs (~7
+        // elements per thread at L = 12, so the staging barrier and the block reduction
+        // are paid over twice the work); longer rows keep 256 threads, where shared
+        // memory, not registers, limits the CTAs per SM.
+        fx_threads = maxDdn <= 1024 ? 128 : 256;
         if (std::is_same<C, double2>::value && !fx) rows = false;   // FP64 rows need the 16-bit table
         if (rows) {
             nblkA = int(maxDup);
@@ -1207,10 +1214,10 @@ static void cf_impl(const CFColumns& P, const View& view, const double* w, int n
                     auto xm = reinterpret_cast<const double2*>(vkm1);
                     auto y = reinterpret_cast<double2*>(wv);
                     if (multi)
-                        k_cf_apply_hub_fx<true><<<g, kApplyThreads, hub_smem, st>>>(view, hv.p, colq.p, x, xm, y, ld, cols.p,
+                        k_cf_apply_hub_fx<true><<<g, fx_threads, hub_smem, st>>>(view, hv.p, colq.p, x, xm, y, ld, cols.p,
                                                                           cf, part.p);
                     else
-                        k_cf_apply_hub_fx<false><<<g, kApplyThreads, hub_smem, st>>>(view, hv.p, colq.p, x, xm, y, ld,
+                        k_cf_apply_hub_fx<false><<<g, fx_threads, hub_smem, st>>>(view, hv.p, colq.p, x, xm, y, ld,
                                                                            cols.p, cf, part.p);
                     done_hub = true;
                 } else if (rows && pair) {
