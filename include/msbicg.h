@@ -220,7 +220,8 @@ msb_status msb_apply_c_up(const msb_model *model, int site, const void *x, void 
  * optional device real vector (NULL: a counter-based pseudo-random vector);
  * `g` is a device real double vector of length dim (caller-owned, output,
  * unit norm).  E_G and residual are host outputs.  Synchronises `stream`.
- * Errors: MSB_EMAXITER if 20 restarts do not reach tol (g, E_G still written). */
+ * Errors: MSB_EMAXITER if 20 restarts do not reach tol (g, E_G still written);
+ * MSB_EINVAL for a direct sum (msb_op_create_direct_sum: take each part's). */
 msb_status msb_ground_state(msb_op *H, double tol, int maxit, const double *start,
                             double *E_G, double *g, double *residual, void *stream);
 
@@ -269,7 +270,9 @@ msb_status msb_multishift_bicg_solve(msb_op *A, msb_complex c0, const void *b,
  * by a Hermitian Lanczos continued fraction of converged depth (see
  * msb_map_params.cf_tol / cf_check / cf_maxdepth).  I_out is a HOST array
  * n_vec x n_w; depth (HOST, nullable) receives each row's depth.
- * The input vectors are not modified.  Synchronises `stream`. */
+ * The input vectors are not modified.  Synchronises `stream`.
+ * Errors: MSB_EINVAL for bad sizes or a direct sum (its columns would mix the
+ * parts; msb_rixs_map_clusters runs one fraction over several clusters). */
 msb_status msb_continued_fraction(msb_op *H, const void *phi, int n_vec, double E0,
                                   const double *w, int n_w, double eta, double cf_tol,
                                   int cf_check, int cf_maxdepth, msb_precision prec,
