@@ -15,6 +15,16 @@ timed steps is bracketed by CUDA events by the library's profiler, which
 gives the dominant kernel's achieved bandwidth / FLOP rate for `roofline`.
 Under torchrun each rank computes the map of its own core site (independent
 problems, no collective on the data path): weak scaling.
+
+Workloads (--workload): hubbard-L12-fp64 (default), hubbard-L8-fp64,
+hubbard-L14-mixed, hubbard-L14-fp64 (the same ring in FP64, for the precision
+comparison; use --n-in to shorten it), hubbard-L12x12rhs-mixed (one right-hand
+side per core site, one call), hubbard-L10-11-12-clusters-mixed (three clusters
+of uneven size in one solve and one continued fraction; its line adds
+`separate_maps`, the same clusters as separate calls), random-csr-fp64 and
+random-csr-mixed (n = 2^22, 256 shifts; one step = the multi-shift solve).
+`cpu_baseline` (the oracle on one host core, a bounded sample scaled to the
+whole map) is sampled for the single-map workloads up to L = 12.
 """
 from __future__ import annotations
 
