@@ -62,3 +62,14 @@ def test_no_device_fails_loudly(lib):
     h = C.c_void_p()
     assert lib.msb_op_create_hubbard(C.byref(m), 0, C.byref(h)) == native.MSB_ECUDA
     assert b"CUDA" in lib.msb_last_error()
+    # the batch entry points refuse the same way (no CPU fallback)
+    parts = (C.c_void_p * 1)(None)
+    assert lib.msb_op_create_direct_sum(parts, None, 1, C.byref(h)) == native.MSB_ECUDA
+    p = native.msb_map_params()
+    lib.msb_map_params_default(C.byref(p))
+    models = (native.msb_model * 2)(m, m)
+    w = (C.c_double * 2)(0.0, 1.0)
+    I = (C.c_double * 8)()
+    info = native.msb_solve_info()
+    assert lib.msb_rixs_map_clusters(models, 2, C.byref(p), w, 2, w, 2, I, None, C.byref(info),
+                                     None) == native.MSB_ECUDA
