@@ -19,11 +19,17 @@ What is computed, and where the paper defines it
   A^dagger space (App. A), used to pin the simplification r~_m = conj(r_m).
 * residual_polynomial: P_m(s) from the seed three-term recurrence (Eqs. C6-C7),
   which the paper equates with zeta_m (Eq. C3).
+* msbicg_reseeded: the adaptive reseeding of App. E around msbicg (the deviation
+  Delta r between the true and the recursive residual of each shift; a rejected
+  shift becomes the next seed).
 
 Parity: pinned by tests/test_oracle_solvers.py (dense eigh and the two-site
 closed form for the ground state; sparse LU vs BiCGStab vs dense solve; the
 MSBiCG solutions against independent solves; zeta_m = P_m(s); collinearity;
-r~ = conj(r); finite termination; the 2x2 toy of Fig. 2c).
+r~ = conj(r); finite termination; the 2x2 toy of Fig. 2c).  msbicg_reseeded: by
+tests/test_oracle_reseeding.py (a no-op on an accurate run; planted round-off in the
+shifted recursions detected by Delta r and repaired by reseeding, checked against
+independent solves; shifts left unconverged by maxit reseeded and solved).
 """
 from __future__ import annotations
 
@@ -171,7 +177,8 @@ def solve_shifted(A: sp.spmatrix, b: np.ndarray, shifts: np.ndarray, tol: float 
 # The multi-shifted BiCG (App. C, Alg. 1), corrected
 # ---------------------------------------------------------------------------
 def msbicg(A, b: np.ndarray, shifts: np.ndarray, tol: float, maxit: int,
-           zeta_sign: float = -1.0, product: str = "bilinear", record: bool = False):
+           zeta_sign: float = -1.0, product: str = "bilinear", record: bool = False,
+           keep_residuals: bool = False, zeta_noise: float = 0.0, noise_seed: int = 0):
     """Solve (A - s_k I) x_k = b for all k from one seed recurrence on A.
 
     A is complex symmetric (A^T = A); `A` may be a sparse matrix or a callable.
@@ -191,7 +198,11 @@ def msbicg(A, b: np.ndarray, shifts: np.ndarray, tol: float, maxit: int,
 
     Returns dict(x=(n_shifts, n), iters=per-shift iteration at freeze,
     converged=bool array, m=iterations, and, if record, the seed scalars and
-    zeta history).
+    zeta history).  keep_residuals adds rrec=(n_shifts, n): each shift's recursive
+    residual r_m / zeta_m (Eq. 4) at its freeze (or at the last iteration).
+    zeta_noise > 0 is a planted fault for tests: each zeta_{m+1} is multiplied by
+    1 + zeta_noise |s| (g1 + i g2) with Gaussian g, an emulation of the round-off
+    that accumulates in the shifted recursions far from the seed (Sec. III, App. E).
     """
     mv = A if callable(A) else (lambda v: A @ v)
     dot = bilinear if product == "bilinear" else hermitian
@@ -210,6 +221,8 @@ def msbicg(A, b: np.ndarray, shifts: np.ndarray, tol: float, maxit: int,
     beta = 0.0 + 0j                                 # beta_0 (p_0 = r_0)
     active = np.ones(ns, dtype=bool)
     iters = np.zeros(ns, dtype=np.int64)
+    rrec = np.zeros((ns, n), dtype=np.complex128) if keep_residuals else None
+    noise = np.random.default_rng(noise_seed) if zeta_noise > 0 else None
     hist = dict(alpha=[], beta=[], zeta=[zeta.copy()], rnorm=[np.linalg.norm(r)])
     m = 0
     # shifts already converged at m = 0 (only if b = 0)
@@ -224,6 +237,9 @@ def msbicg(A, b: np.ndarray, shifts: np.ndarray, tol: float, maxit: int,
         idx = np.nonzero(active)[0]
         zeta_next = ((1 + zeta_sign * alpha * s[idx]) * zeta[idx]
                      + (alpha * beta / alpha_prev) * (zeta[idx] - zeta_prev[idx]))
+        if noise is not None:
+            g = noise.standard_normal(len(idx)) + 1j * noise.standard_normal(len(idx))
+            zeta_next = zeta_next * (1 + zeta_noise * np.abs(s[idx]) * g)
         if np.any(zeta_next == 0):
             raise ZeroDivisionError("shift breakdown: zeta_{m+1} = 0")
         alpha_s = (zeta[idx] / zeta_next) * alpha
@@ -242,15 +258,73 @@ def msbicg(A, b: np.ndarray, shifts: np.ndarray, tol: float, maxit: int,
         rn = np.linalg.norm(r)
         iters[idx] = m
         done = rn / np.abs(zeta[idx]) <= tol * nb
+        if keep_residuals:
+            rrec[idx[done]] = r[None, :] / zeta[idx[done], None]
         active[idx[done]] = False
         if record:
             hist["alpha"].append(alpha); hist["beta"].append(beta)
             hist["zeta"].append(zeta.copy()); hist["rnorm"].append(rn)
     converged = ~active | (rn == 0)
     out = dict(x=x, iters=iters, converged=converged, m=m, r=r, zeta=zeta)
+    if keep_residuals:
+        rest = np.nonzero(active)[0]
+        rrec[rest] = r[None, :] / zeta[rest, None]
+        out["rrec"] = rrec
     if record:
         out["hist"] = hist
     return out
+
+
+def msbicg_reseeded(A, b: np.ndarray, shifts: np.ndarray, tol: float, maxit: int, reseed_tol: float,
+                    seed_index: int = 0, max_seeds: int = 8, **kw):
+    """Adaptive reseeding (App. E) around msbicg.
+
+    Solve (A - s_k I) x_k = b for all k.  Start from the seed system A - s_{seed} I.
+    After a run, compare for every shift the true residual r_t = b - (A - s_k I) x_k (one
+    MVM per shift) with the recursive residual r / zeta that MSBiCG carried (Eq. 4):
+    Delta r_k = ||r_t - r / zeta||.  A shift whose Delta r_k exceeds reseed_tol ||b||, or
+    that did not converge within maxit, is not accepted.  The rejected shift closest to
+    the current seed becomes the next seed, and the rejected shifts are solved again
+    from it; accepted shifts keep their solution.  Stops when every shift is accepted or
+    after max_seeds seeds.  Reading of "promote the corresponding w_in": with several
+    rejected shifts, the one next to the seed's accurate region (closest to the seed),
+    as in the paper's example (seed -4t, then 0).
+
+    Returns dict(x, seeds=list of seed indices, dr=Delta r per shift (last run that
+    solved it), accepted=bool array, runs=list of (seed, shifts solved)).
+    """
+    mv = A if callable(A) else (lambda v: A @ v)
+    s = np.asarray(shifts, dtype=np.complex128)
+    b = np.asarray(b, dtype=np.complex128)
+    ns, n = len(s), len(b)
+    nb = np.linalg.norm(b)
+    x = np.zeros((ns, n), dtype=np.complex128)
+    dr = np.full(ns, np.inf)
+    accepted = np.zeros(ns, dtype=bool)
+    seeds, runs = [], []
+    todo = np.arange(ns)
+    s0 = int(seed_index)
+    while todo.size and len(seeds) < max_seeds:
+        seeds.append(s0)
+        runs.append((s0, todo.copy()))
+        sigma = s[s0]
+        res = msbicg(lambda v, sigma=sigma: mv(v) - sigma * v, b, s[todo] - sigma, tol, maxit,
+                     keep_residuals=True, **kw)
+        rejected = []
+        for j, k in enumerate(todo):
+            xk = res["x"][j]
+            rt = b - (mv(xk) - s[k] * xk)
+            dr[k] = np.linalg.norm(rt - res["rrec"][j])
+            x[k] = xk
+            ok = bool(res["converged"][j]) and dr[k] <= reseed_tol * nb
+            accepted[k] = ok
+            if not ok:
+                rejected.append(int(k))
+        if not rejected:
+            break
+        s0 = min(rejected, key=lambda k: abs(s[k] - sigma))
+        todo = np.array(rejected)
+    return dict(x=x, seeds=seeds, dr=dr, accepted=accepted, runs=runs)
 
 
 def residual_polynomial(alphas, betas, z: complex, m: int) -> complex:
