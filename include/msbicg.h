@@ -349,6 +349,20 @@ msb_status msb_rixs_map_clusters(const msb_model *models, int n_clusters, const 
                                  const double *w_in, int n_in, const double *w, int n_w, double *I_out,
                                  double *E_G_out, msb_solve_info *info, void *stream);
 
+/* Momentum-resolved maps (the coherent sum over core sites, Sec. III): for every
+ * site j the map of msb_rixs_map_sites is formed up to phi_j = c_{j,up} Psi_j
+ * (one ground state; one multi-shift solve per site on that site's H'), then
+ *   phi_q = sum_j exp(i q j) phi_j   and
+ *   I_q(w_in, w) = (1/pi) Im <phi_q|(H - E_G - w - i eta)^{-1}|phi_q>
+ * by one continued fraction over all n_q * n_in columns.  qs: HOST array of
+ * n_q momenta (radians per site; over q = 2 pi k / L the maps sum to L times the
+ * sum of the single-site maps).  model->core_site is ignored.  I_out: HOST array
+ * n_q x n_in x n_w (q slowest).  Requires n_q * n_in <= 65535 and
+ * L * n_in <= 65535.  Synchronises `stream`.  Errors as msb_rixs_map. */
+msb_status msb_rixs_map_q(const msb_model *model, const msb_map_params *params, const double *qs, int n_q,
+                          const double *w_in, int n_in, const double *w, int n_w, double *I_out,
+                          msb_solve_info *info, void *stream);
+
 /* Same map with the operators already built and the result left on the
  * device: H = msb_op_create_hubbard(model, 0), Hp = msb_op_create_hubbard(model,
  * 1) of one model (checked); w_in, w are HOST grids (copied in); I_dev is a

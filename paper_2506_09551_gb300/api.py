@@ -235,6 +235,21 @@ def rixs_map_sites(m: N.msb_model, params: N.msb_map_params, sites, w_in, w, all
     return I, info.as_dict(), st
 
 
+def rixs_map_q(m: N.msb_model, params: N.msb_map_params, qs, w_in, w, allow_status=(N.MSB_EMAXITER,)):
+    """Momentum-resolved maps I[n_q, n_in, n_w] (coherent sum over core sites), info, status."""
+    qs = np.ascontiguousarray(qs, dtype=np.float64)
+    w_in = np.ascontiguousarray(w_in, dtype=np.float64)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    I = np.zeros((len(qs), len(w_in), len(w)), dtype=np.float64)
+    info = N.msb_solve_info()
+    st = N.load().msb_rixs_map_q(C.byref(m), C.byref(params), qs.ctypes.data_as(C.POINTER(C.c_double)), len(qs),
+                                 w_in.ctypes.data_as(C.POINTER(C.c_double)), len(w_in),
+                                 w.ctypes.data_as(C.POINTER(C.c_double)), len(w),
+                                 I.ctypes.data_as(C.POINTER(C.c_double)), C.byref(info), _stream())
+    N.check(st, allow=allow_status)
+    return I, info.as_dict(), st
+
+
 def rixs_map_clusters(models, params: N.msb_map_params, w_in, w, allow_status=(N.MSB_EMAXITER,)):
     """Maps of several independent clusters computed together (one solve on their direct
     sum, one continued fraction over all columns): I[n_clusters, n_in, n_w] (numpy),

@@ -309,9 +309,33 @@ namespace msb {
 // Maps of several core sites of one model (one right-hand side O2 = c^dag_{j,up}
 // per site): one ground state, one solve per site on its own H', then one
 // continued fraction over all sites' columns, since H is the same for all.
+// phi_q = sum_j exp(i q site_j) phi_j for every momentum q, incident energy and
+// element: out[q][r] = sum_j ph[q][j] phi[j][r], r < per_site (= n_in * D).
+template <typename C>
+__global__ void __launch_bounds__(256) k_qsum(const C* __restrict__ phi, int n_sites, int64_t per_site,
+                                              const double2* __restrict__ ph, int n_q, C* __restrict__ out) {
+    using S = scalar_t<C>;
+    const int64_t n = int64_t(n_q) * per_site;
+    for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < n; e += int64_t(gridDim.x) * blockDim.x) {
+        const int q = int(e / per_site);
+        const int64_t r = e - int64_t(q) * per_site;
+        S ax = S(0), ay = S(0);
+        for (int j = 0; j < n_sites; ++j) {
+            const double2 p = ph[int64_t(q) * n_sites + j];
+            const C v = phi[int64_t(j) * per_site + r];
+            ax += S(p.x) * v.x - S(p.y) * v.y;
+            ay += S(p.x) * v.y + S(p.y) * v.x;
+        }
+        out[e] = mk(ax, ay);
+    }
+}
+
+// Maps of several core sites (n_q = 0: one map per site), or their coherent sums
+// over the sites with momentum phases (n_q > 0: one map per q, Sec. III).
 static void rixs_map_sites_impl(const msb_model& m, const msb_map_params& prm, const int* sites, int n_sites,
                                 const double* w_in, int n_in, const double* w, int n_w, double* I_out,
-                                msb_solve_info& info, cudaStream_t st) {
+                                msb_solve_info& info, cudaStream_t st, const double* qs = nullptr,
+                                int n_q = 0) {
     validate_model(m);
     MSB_REQUIRE(sites != nullptr && n_sites >= 1, "need at least one site");
     MSB_REQUIRE(n_in >= 1 && n_in <= kMaxShifts && int64_t(n_sites) * n_in <= 65535,
@@ -355,10 +379,39 @@ static void rixs_map_sites_impl(const msb_model& m, const msb_map_params& prm, c
                                           Phi.p + size_t(i) * n_in * D * csz, info, st, launches);
         maxit_hit |= sst == MSB_EMAXITER;
     }
+    const void* cf_in = Phi.p;
+    int n_cols = n_sites * n_in;
+    DevBuf<char> Phiq;
+    if (n_q > 0) {
+        std::vector<double2> ph(size_t(n_q) * n_sites);
+        for (int q = 0; q < n_q; ++q)
+            for (int j = 0; j < n_sites; ++j)
+                ph[size_t(q) * n_sites + j] = make_double2(std::cos(qs[q] * sites[j]), std::sin(qs[q] * sites[j]));
+        DevBuf<double2> dph(ph.size());
+        dph.upload(ph.data(), ph.size(), st);
+        const int64_t per_site = int64_t(n_in) * D;
+        Phiq.alloc(size_t(n_q) * per_site * csz);
+        const int g = grid_for(int64_t(n_q) * per_site, 256, 8);
+        {
+            ProfScope ps("sector_map", st, double(n_q) * per_site * csz * (n_sites + 1), 8.0 * n_q * per_site * n_sites);
+            if (prm.precision == MSB_FP64)
+                k_qsum<double2><<<g, 256, 0, st>>>((const double2*)Phi.p, n_sites, per_site, dph.p, n_q,
+                                                   (double2*)Phiq.p);
+            else
+                k_qsum<float2><<<g, 256, 0, st>>>((const float2*)Phi.p, n_sites, per_site, dph.p, n_q,
+                                                  (float2*)Phiq.p);
+        }
+        MSB_LAUNCH_CHECK();
+        MSB_CUDA(cudaStreamSynchronize(st));
+        ++launches;
+        Phi.release();
+        cf_in = Phiq.p;
+        n_cols = n_q * n_in;
+    }
     info.seconds_solve = secs(t0);
     t0 = std::chrono::steady_clock::now();
     CFResult cr;
-    continued_fraction(opH.get(), Phi.p, n_sites * n_in, gr.E, w, n_w, prm.eta, prm.cf_tol, prm.cf_check,
+    continued_fraction(opH.get(), cf_in, n_cols, gr.E, w, n_w, prm.eta, prm.cf_tol, prm.cf_check,
                        prm.cf_maxdepth, prm.precision, I_out, cr, st, false);
     launches += cr.launches;
     info.matvecs += cr.matvecs;
@@ -588,6 +641,32 @@ extern "C" msb_status msb_rixs_map_sites(const msb_model* model, const msb_map_p
             ~Fill() { if (dst) { src->device_bytes = msb::g_alloc_bytes; *dst = *src; } }
         } fill{info, &local};
         msb::rixs_map_sites_impl(*model, *params, sites, n_sites, w_in, n_in, w, n_w, I_out, local, scope.s);
+        scope.finish();
+        msb::prof_collect();
+    });
+}
+
+extern "C" msb_status msb_rixs_map_q(const msb_model* model, const msb_map_params* params, const double* qs, int n_q,
+                                     const double* w_in, int n_in, const double* w, int n_w, double* I_out,
+                                     msb_solve_info* info, void* stream) {
+    if (info) *info = msb_solve_info{};
+    return msb::guard("msb_rixs_map_q", [&] {
+        msb::require_device();
+        MSB_REQUIRE(model != nullptr && params != nullptr && qs != nullptr, "NULL argument");
+        MSB_REQUIRE(n_q >= 1 && int64_t(n_q) * n_in <= 65535, "need 1 <= n_q and n_q * n_in <= 65535");
+        for (int q = 0; q < n_q; ++q) MSB_REQUIRE(std::isfinite(qs[q]), "momenta must be finite");
+        msb::validate_model(*model);
+        std::vector<int> sites(model->L);
+        for (int j = 0; j < model->L; ++j) sites[j] = j;
+        msb::g_alloc_bytes = 0;
+        msb_solve_info local{};
+        msb::StreamScope scope((cudaStream_t)stream);
+        struct Fill {
+            msb_solve_info* dst; msb_solve_info* src;
+            ~Fill() { if (dst) { src->device_bytes = msb::g_alloc_bytes; *dst = *src; } }
+        } fill{info, &local};
+        msb::rixs_map_sites_impl(*model, *params, sites.data(), model->L, w_in, n_in, w, n_w, I_out, local, scope.s,
+                                 qs, n_q);
         scope.finish();
         msb::prof_collect();
     });

@@ -88,6 +88,8 @@ SIGNATURES = {
                                 _PD, _I, _PD, C.POINTER(msb_solve_info), _P]),
     "msb_rixs_map_clusters": (_I, [C.POINTER(msb_model), _I, C.POINTER(msb_map_params), _PD, _I, _PD, _I, _PD,
                                    _PD, C.POINTER(msb_solve_info), _P]),
+    "msb_rixs_map_q": (_I, [C.POINTER(msb_model), C.POINTER(msb_map_params), _PD, _I, _PD, _I, _PD, _I, _PD,
+                            C.POINTER(msb_solve_info), _P]),
     "msb_profile_enable": (None, [_I]),
     "msb_profile_reset": (None, []),
     "msb_profile_read": (_I, [C.POINTER(msb_kernel_stat), _I]),
