@@ -52,9 +52,12 @@ WORKLOADS = {
     "hubbard-L14-fp64": (workloads.CHAIN14, 0, 1e-10, 1e-10),
     "hubbard-L8-fp64": (workloads.CHAIN8, 0, 1e-10, 1e-10),
     "hubbard-L12x12rhs-mixed": (workloads.BATCH_SITES, 1, 1e-8, 1e-8),
+    "hubbard-L12-q12-mixed": (workloads.BATCH_SITES, 1, 1e-8, 1e-8),
 }
 # workloads with one right-hand side per core site (one call, one shared second step)
 SITES = {"hubbard-L12x12rhs-mixed": list(range(12))}
+# momentum-resolved maps (coherent sum over all core sites): name -> number of momenta 2 pi k / L
+QMAPS = {"hubbard-L12-q12-mixed": 12}
 # clusters of uneven size in one call: name -> (clusters, precision, solve_tol, cf_tol)
 CLUSTERS = {"hubbard-L10-11-12-clusters-mixed": (workloads.BATCH_CLUSTERS, 1, 1e-8, 1e-8)}
 DEFAULT = "hubbard-L12-fp64"
@@ -401,7 +404,12 @@ def gpu_arm(args, rank, world):
     lib = native.load()
     sites = SITES.get(args.workload)
 
+    n_q = QMAPS.get(args.workload, 0)
+    qs = 2 * np.pi * np.arange(n_q) / wl.L if n_q else None
+
     def one_map():
+        if n_q:
+            return api.rixs_map_q(m, p, qs, w_in, w)
         if clusters:
             I, E, info, st = api.rixs_map_clusters(models, p, w_in, w)
             return I, info, st
@@ -440,7 +448,7 @@ def gpu_arm(args, rank, world):
     ms = e0.elapsed_time(e1) / args.steps
     clocks = clk.summary()
     ms = max_over_ranks(ms, world)          # whole-job time = the slowest rank's
-    n_maps = len(clusters) if clusters else (len(sites) if sites else 1)
+    n_maps = len(clusters) if clusters else (len(sites) if sites else (n_q or 1))
     pts = len(w_in) * len(w) * n_maps
     value = job_throughput(pts, world, ms * 1e-3)
 
@@ -452,7 +460,7 @@ def gpu_arm(args, rank, world):
     I_host = None
     if args.no_e2e:
         pass
-    elif sites or clusters:
+    elif sites or clusters or n_q:
         one_map()          # already the host API: grids in from the host, maps out to the host
     else:
         I_host, info_e2e, _ = api.rixs_map(m, p, w_in, w)
