@@ -21,7 +21,9 @@ hubbard-L14-mixed, hubbard-L14-fp64 (the same ring in FP64, for the precision
 comparison; use --n-in to shorten it), hubbard-L12x12rhs-mixed (one right-hand
 side per core site, one call), hubbard-L10-11-12-clusters-mixed (three clusters
 of uneven size in one solve and one continued fraction; its line adds
-`separate_maps`, the same clusters as separate calls), random-csr-fp64 and
+`separate_maps`, the same clusters as separate calls), hubbard-L12-q12-mixed
+(momentum-resolved maps: the coherent sum over the 12 core sites at the 12
+momenta 2 pi k / 12), random-csr-fp64 and
 random-csr-mixed (n = 2^22, 256 shifts; one step = the multi-shift solve).
 `cpu_baseline` (the oracle on one host core, a bounded sample scaled to the
 whole map) is sampled for the single-map workloads up to L = 12.
