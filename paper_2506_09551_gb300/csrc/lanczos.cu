@@ -482,7 +482,11 @@ constexpr int kMaxHops = 16;
 // column are adjacent in launch order, so the column being gathered from stays
 // in L2; V_{k-1} and W are streamed with evict-first hints so they do not push
 // it out.  Offsets inside a column are 32-bit (fewer than 2^31 elements for
-// L <= 16).
+// L <= 16).  Three variants follow: this one (FP32 rows with an odd D_dn, one
+// element per thread), k_cf_apply_hub_fx (FP64, hop sums in fixed point) and
+// k_cf_apply_hub_f2x2 (FP32, two elements per thread, bank-aware placement).
+// Multi: the columns belong to clusters of different sizes; each CTA reads its
+// column's cluster view, and CTAs past that cluster's rows write a zero partial.
 template <typename C, bool Multi>
 __global__ void __launch_bounds__(256, 6) k_cf_apply_hub(HubView h0, const HubView* __restrict__ hv,
                                                          const int* __restrict__ colq, const C* __restrict__ Vk,
@@ -773,7 +777,12 @@ __global__ void __launch_bounds__(256, 5) k_cf_apply_hub_fx(HubView h0, const Hu
 // FP32 pass A with two adjacent elements per thread: the up-spin gathers, the
 // V_{k-1} loads and the W stores move 16 bytes (two complex floats) at a time,
 // and the down-spin table is read as 16-bit entries, two per 32-bit load.
-// Needs an even Ddn (rows start on 16-byte boundaries) and Ddn < 32768.
+// Needs an even Ddn (rows start on 16-byte boundaries) and Ddn < 32768.  The row
+// sits at the sector's bank-aware slots (slot16, with the table hdn16p rewritten
+// to them) when the operator has them; the down-spin loop runs to the warp's
+// largest hop count, empty slots reading the zero kept past the row.  No FP64
+// instruction: coefficients arrive as FP32 copies, the product is compensated
+// FP32, and the block sum is float-float.
 template <bool Multi>
 __global__ void __launch_bounds__(256, 6) k_cf_apply_hub_f2x2(HubView h0, const HubView* __restrict__ hv,
                                                               const int* __restrict__ colq,
