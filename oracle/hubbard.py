@@ -21,7 +21,9 @@ The spectrum I(w_in, w) must not depend on the ordering; the tests use that.
 
 Parity: every function here is pinned by tests/test_oracle_model.py (sector
 sizes, Hermiticity, the U=0 spectrum against single-particle energies, the
-two-site closed form, O1 = O2^T).
+two-site closed form, O1 = O2^T).  hamiltonian_kron, the Kronecker-sum assembly
+used for the large sectors (L = 14) of the full-size parity tests, is pinned
+there as equal to the generic construction entry by entry.
 """
 from __future__ import annotations
 
@@ -174,6 +176,49 @@ def hamiltonian(sec: Sector, t: float, U: float, Uc: float = 0.0, core_site: int
     H.sum_duplicates()
     H.eliminate_zeros()
     return H
+
+
+def species_hops(L: int, n: int, t: float, periodic: bool = True) -> sp.csr_matrix:
+    """Hopping matrix of one spin species alone: -t sum_<ij> (c^dag_j c_i + h.c.)
+    on the L-bit strings with n set bits (rank order), with the textbook
+    Jordan-Wigner sign computed by `annihilate` / `create` on those strings."""
+    states = sector_states(L, n)
+    rank = np.full(1 << L, -1, dtype=np.int64)
+    rank[states] = np.arange(len(states))
+    R, C, V = [], [], []
+    for (i, j) in bonds(L, periodic):
+        for (a, b) in ((i, j), (j, i)):
+            a1, s1, mid = annihilate(states, a)
+            a2, s2, new = create(mid, b)
+            ok = a1 & a2
+            R.append(rank[new[ok]]); C.append(np.nonzero(ok)[0]); V.append(-t * (s1 * s2)[ok])
+    D = len(states)
+    T = sp.coo_matrix((np.concatenate(V), (np.concatenate(R), np.concatenate(C))), shape=(D, D)).tocsr()
+    T.sum_duplicates()
+    return T
+
+
+def hamiltonian_kron(sec: Sector, t: float, U: float, Uc: float = 0.0, core_site: int | None = None,
+                     periodic: bool = True) -> sp.csr_matrix:
+    """The same H (Eq. 9, plus the core-hole term of Eq. 10) assembled as
+    T_up (x) I + I (x) T_dn + diag.  With the "up-first" orbital order every
+    orbital strictly between two up orbitals is an up orbital (and likewise for
+    down), so a hop's Jordan-Wigner sign involves its own species only and each
+    hop term factorises into one species' hop matrix times the identity on the
+    other.  A faster construction for large sectors; equal to `hamiltonian`
+    entry by entry (pinned in tests/test_oracle_model.py)."""
+    if sec.order != "up-first":
+        raise ValueError("the Kronecker form needs the up-first orbital order")
+    Tu = species_hops(sec.L, sec.n_up, t, periodic)
+    Td = species_hops(sec.L, sec.n_dn, t, periodic)
+    diag = U * popcount(sec.u & sec.d).astype(np.float64)
+    if core_site is not None:
+        diag -= Uc * (sec.occupation(core_site, 0) + sec.occupation(core_site, 1))
+    H = (sp.kron(Tu, sp.identity(sec.D_dn), format="csr") + sp.kron(sp.identity(sec.D_up), Td, format="csr")
+         + sp.diags(diag, format="csr"))
+    H.sum_duplicates()
+    H.eliminate_zeros()
+    return H.tocsr()
 
 
 def creation_operator(src: Sector, dst: Sector, site: int, spin: int) -> sp.csr_matrix:

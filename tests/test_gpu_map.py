@@ -107,27 +107,6 @@ def test_translation_and_spin_invariance(cuda):
         assert orixs.relative_l2(I, maps[0]) <= 1e-9
 
 
-def test_chain12_sampled_rows(cuda):
-    """The L = 12 workload at full size on the GPU; the oracle recomputes two rows
-    (the seed row and the far end of the grid) by independent solves."""
-    from paper_2506_09551_gb300 import api
-    wl = workloads.CHAIN12
-    I, info, st = api.rixs_map(api.model(wl.L, wl.n_up, wl.n_dn), _params(api, solve_tol=1e-10, cf_tol=1e-10),
-                               wl.w_in, wl.w)
-    assert st == 0 and info["n_converged"] == wl.n_in
-    om = hubbard.RixsModel(wl.L, wl.n_up, wl.n_dn, 1.0, 8.0, 4.0, 0)
-    E_G, G, _ = solvers.ground_state(om.H, workloads.lanczos_start(om.H.shape[0], 1), kmax=250)
-    assert abs(info["E_G"] - E_G) <= 1e-11 * abs(E_G)
-    n = om.Hp.shape[0]
-    A = (om.Hp - (E_G + 1j * wl.Gamma) * sp.identity(n)).tocsr()
-    E = om.O2 @ G
-    for k in (workloads.seed_index(wl.w_in), wl.n_in - 1):
-        X, _ = solvers.solve_shifted(A, E, np.array([wl.w_in[k]]), tol=1e-12, method="bicgstab")
-        I_ref, _ = spectrum.lanczos_cf(om.H, om.O1 @ X[0], E_G, wl.w, wl.eta, cf_tol=1e-12)
-        err = np.linalg.norm(I[k] - I_ref) / np.linalg.norm(I_ref)
-        assert err <= 1e-8, (k, err)
-
-
 def test_map_sites_batched_right_hand_sides(cuda, chain8_oracle):
     """One call for every core site of the L = 8 ring (the batched workload's shape):
     each site's map equals the single-site call, all sites agree by translation

@@ -105,3 +105,16 @@ def test_o1_is_o2_transpose_and_anticommutator(order):
     cd_back = hubbard.creation_operator(lower, mid, 3, 0)
     anti = (m.O1 @ m.O2 + cd_back @ c_dn_to).toarray()
     assert np.allclose(anti, np.eye(mid.dim))
+
+
+@pytest.mark.parametrize("L,nu,nd,core,periodic", [(8, 4, 4, None, True), (8, 5, 4, 0, True),
+                                                   (7, 3, 2, 2, False), (9, 5, 4, 4, True), (6, 0, 3, None, True)])
+def test_kronecker_form_equals_generic_construction(L, nu, nd, core, periodic):
+    """hamiltonian_kron (per-species hop matrices in a Kronecker sum, used for the large
+    sectors of the full-size parity tests) equals the generic Jordan-Wigner construction
+    entry by entry, with and without the core hole, on rings and open chains."""
+    sec = hubbard.Sector(L, nu, nd)
+    A = hubbard.hamiltonian(sec, 1.0, 8.0, 4.0, core, periodic)
+    B = hubbard.hamiltonian_kron(sec, 1.0, 8.0, 4.0, core, periodic)
+    assert A.shape == B.shape and A.nnz == B.nnz
+    assert abs(A - B).max() == 0.0
