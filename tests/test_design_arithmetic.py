@@ -1,4 +1,4 @@
-"""CPU pins of two arithmetic schemes the GPU path uses in place of the plain forms.
+"""CPU pins of three arithmetic schemes the GPU path uses in place of the plain forms.
 
 1. The continued fraction is carried forward level by level (modified Lentz
    recurrences) instead of being re-evaluated bottom-up at every convergence check.
@@ -7,7 +7,14 @@
 2. The FP64 Hamiltonian apply of the continued fraction sums its +-1 hop terms in 64-bit
    integer fixed point scaled by the column norm.  Here the conversion is emulated bit for
    bit in Python integers and its claimed properties are checked: |F| < 2^58, a loss below
-   2^-55 ||V|| per term, exact sums of up to 2L terms, zeros and subnormals mapped to 0."""
+   2^-55 ||V|| per term, exact sums of up to 2L terms, zeros and subnormals mapped to 0.
+3. The FP32-mixed path forms its inner products (the bilinear products of the seed
+   recurrence, the norms and the Lanczos products of the second step) from FP32 vectors
+   with no FP64 instruction per element: each thread accumulates x*y as an unevaluated
+   float pair (hi, lo), the product split exactly by an FMA (TwoProduct) and added by
+   Knuth's TwoSum; the pairs are then summed in float-float and rounded to FP64 once.
+   Emulated here with IEEE float32 numpy operations and checked against the exact FP64
+   dot of the same FP32 data: relative error <= n 2^-46 * sum|x y| / |sum x y|."""
 import math
 import struct
 
@@ -106,3 +113,60 @@ def test_fixed_point_zero_and_nonfinite_map_to_zero():
     assert _fx(0.0, eB) == 0 and _fx(-0.0, eB) == 0
     assert _fx(5e-324, eB) == 0                  # subnormal
     assert _fx(float("inf"), eB) == 0 and _fx(float("nan"), eB) == 0
+
+
+# ---------------------------------------------------------------------------
+# 3. float-float products of the FP32 path
+# ---------------------------------------------------------------------------
+_f32 = np.float32
+
+
+def _two_prod(x, y):
+    p = _f32(x * y)
+    # the exact product of two float32 values is a float64; its rounding error is a float32
+    pe = _f32(np.float64(x) * np.float64(y) - np.float64(p))
+    return p, pe
+
+
+def _df_add_prod(hi, lo, x, y):
+    p, pe = _two_prod(x, y)
+    s = _f32(hi + p)
+    bb = _f32(s - hi)
+    e = _f32(_f32(hi - _f32(s - bb)) + _f32(p - bb))
+    return s, _f32(lo + _f32(e + pe))
+
+
+def _df_add(hi, lo, bh, bl):
+    s = _f32(hi + bh)
+    bb = _f32(s - hi)
+    e = _f32(_f32(hi - _f32(s - bb)) + _f32(bh - bb))
+    return s, _f32(lo + _f32(e + bl))
+
+
+@pytest.mark.parametrize("n,threads,signed", [(4096, 256, False), (20000, 256, True), (777, 32, True)])
+def test_float_float_dot_against_fp64(n, threads, signed):
+    rng = np.random.default_rng(n)
+    x = rng.standard_normal(n).astype(np.float32)
+    y = rng.standard_normal(n).astype(np.float32)
+    if not signed:
+        y = np.abs(y) * np.sign(x)                      # all products positive: no cancellation
+    # per-thread pairs over a grid-stride loop, then the pairs summed in float-float
+    pairs = []
+    for t in range(threads):
+        hi, lo = _f32(0), _f32(0)
+        for i in range(t, n, threads):
+            hi, lo = _df_add_prod(hi, lo, x[i], y[i])
+        pairs.append((hi, lo))
+    hi, lo = _f32(0), _f32(0)
+    for bh, bl in pairs:
+        hi, lo = _df_add(hi, lo, bh, bl)
+    got = np.float64(hi) + np.float64(lo)
+    exact = math.fsum(float(np.float64(a) * np.float64(b)) for a, b in zip(x, y))
+    mag = math.fsum(abs(float(np.float64(a) * np.float64(b))) for a, b in zip(x, y))
+    bound = n * 2.0 ** -46 * mag
+    assert abs(got - exact) <= bound, (got, exact, bound)
+    # and far better than a plain FP32 sum
+    plain = _f32(0)
+    for a, b in zip(x, y):
+        plain = _f32(plain + _f32(a * b))
+    assert abs(got - exact) <= 1e-3 * max(abs(float(plain) - exact), 1e-300) or abs(got - exact) <= 1e-12 * mag
