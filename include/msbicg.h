@@ -143,15 +143,27 @@ msb_status msb_basis_states(const msb_basis *b, int species, uint32_t *out);
 
 void msb_basis_destroy(msb_basis *b);
 
+/* Row order of the continued fraction (second step of Eq. 1).  That step needs
+ * only the Lanczos coefficients, so its internal vectors may hold each row's
+ * down-spin states in any fixed order.  The row-tiled apply kernels run their
+ * down-spin loop to the largest hop count among a warp's elements, so position
+ * p of a row holds down state order[p], the states sorted by their number of
+ * down-spin hops (descending, ties in rank order).  No effect on any result.
+ * Host only, no device.  order: HOST array of D_dn entries (a permutation of
+ * 0..D_dn-1).  Errors: MSB_EINVAL if D_dn is not below 32768, or periodic with
+ * L < 3. */
+msb_status msb_basis_row_order(const msb_basis *b, int periodic, uint16_t *order);
+
 /* Shared-memory placement of a down-spin row used by the FP32 continued-fraction
- * apply.  That kernel stages each row of a vector in shared memory and gathers
- * the down-spin hop targets from it; since the hop table is the same for every
- * row, the library places element d at a slot chosen once per sector, so that
- * the gathers of a half-warp hit fewer shared-memory bank conflicts (a
- * deterministic hill climb; no effect on any result).  Host only, no device.
- * slot: HOST array of D_dn entries (may be NULL): slot[d] for each down state
- * d (a permutation of 0..D_dn-1).  cost_plain / cost_layout (may be NULL): the
- * mean worst-bank count per half-warp gather for slot[d] = d and for the
+ * apply.  That kernel stages each row of a vector in shared memory (in the row
+ * order above) and gathers the down-spin hop targets from it; since the hop
+ * table is the same for every row, the library places position p at a slot
+ * chosen once per sector, so that the gathers of a half-warp hit fewer
+ * shared-memory bank conflicts (a deterministic hill climb; no effect on any
+ * result).  Host only, no device.
+ * slot: HOST array of D_dn entries (may be NULL): slot[p] for each position p
+ * (a permutation of 0..D_dn-1).  cost_plain / cost_layout (may be NULL): the
+ * mean worst-bank count per half-warp gather for slot[p] = p and for the
  * chosen slots (1 is conflict free).  Errors: MSB_EINVAL if D_dn is odd or
  * not below 32768, or periodic with L < 3. */
 msb_status msb_basis_row_layout(const msb_basis *b, int periodic, uint16_t *slot, double *cost_plain,
@@ -225,17 +237,22 @@ msb_status msb_apply_c_up(const msb_model *model, int site, const void *x, void 
 msb_status msb_ground_state(msb_op *H, double tol, int maxit, const double *start,
                             double *E_G, double *g, double *residual, void *stream);
 
-/* The same ground state for callers that cannot allocate device memory
- * (code running inside a stream capture in global capture mode, or a host
- * whose device memory is owned by another allocator under a fixed budget).
+/* The same ground state for callers that cannot allocate device memory: a
+ * process whose device memory is owned by another allocator under a fixed
+ * budget (a framework's caching pool, a server that reserved its memory at
+ * start-up), where one more cudaMalloc fails or fragments that budget.
  * The paper has no counterpart: this is a deployment variant.  It allocates
- * nothing: its scratch is a fixed array inside the library image (about 40
- * MB, held on every GPU that loads the library until the process exits).
- * Limits: dim <= 1048576 (2^20) and maxit <= 1024, else MSB_EINVAL.  The
- * first call on each device looks up the array's address, so make that first
- * call before any stream capture.  Work is ordered on `stream` itself, which
- * is synchronised before returning.  All calls share the array: calls that
- * overlap on the GPU race.  Arguments and results as msb_ground_state. */
+ * nothing: its scratch is a fixed array inside the library image of
+ * 5 * 2^20 doubles plus a few KB (about 42 MB), held on every GPU that loads
+ * the library until the process exits.  Limits: dim <= 1048576 (2^20) and
+ * maxit <= 1024, else MSB_EINVAL.  The array's device address is looked up at
+ * the start of every call, on the caller's current device.  Work is ordered on
+ * `stream` itself; the call synchronises `stream` and copies the Lanczos
+ * coefficients to the host at every step, and returns after a final
+ * synchronisation.  All calls share the array and it keeps the previous
+ * call's contents (every part a call reads is written first in that call):
+ * calls that overlap on the GPU race.  Arguments and results as
+ * msb_ground_state. */
 msb_status msb_ground_state_noalloc(msb_op *H, double tol, int maxit, const double *start,
                                     double *E_G, double *g, double *residual, void *stream);
 
@@ -259,6 +276,42 @@ msb_status msb_multishift_bicg_solve(msb_op *A, msb_complex c0, const void *b,
                                      int maxit, int block, msb_precision prec, void *x,
                                      int *iters, double *resid, int *converged,
                                      msb_solve_info *info, void *stream);
+
+/* Adaptive reseeding (App. E, Fig. 5) around the solve above.  Solves
+ * (A + c0 I - s_k I) x_k = b for every shift, first from the seed system
+ * A + c0 - s_{seed_index}.  After each run, every solved shift's true residual
+ * b - (A + c0 - s_k) x_k (one operator application per shift) is compared with
+ * the recursive residual r_m / zeta_m^k the recurrence carried (Eq. 4):
+ * dr[k] = ||true - recursive||.  A shift is accepted when it converged and
+ * dr[k] <= reseed_tol ||b||.  The rejected shift closest to the current seed
+ * becomes the next seed and the rejected shifts are solved again from it;
+ * accepted shifts keep their solutions.  Stops when all are accepted or after
+ * max_seeds seeds.  x: device block of n_shifts vectors (output).  HOST
+ * outputs (may be NULL): converged[k], accepted[k], dr[k] (of the last run that
+ * solved shift k), seeds[max_seeds] (the seed indices used, in order) and
+ * *n_seeds.  info->iterations and ->matvecs sum over the runs.  Returns
+ * MSB_EMAXITER (results written) if some shift is not accepted, MSB_ENONFINITE
+ * on a failed recurrence.  Allocates two n_shifts x dim work blocks. */
+msb_status msb_multishift_bicg_reseeded(msb_op *A, msb_complex c0, const void *b, const msb_complex *shifts,
+                                        int n_shifts, double tol, int maxit, int block, msb_precision prec,
+                                        double reseed_tol, int seed_index, int max_seeds, void *x, int *converged,
+                                        int *accepted, double *dr, int *seeds, int *n_seeds, msb_solve_info *info,
+                                        void *stream);
+
+/* The paper's baseline for Eq. 2 (Sec. III, Fig. 4): every shift solved on its
+ * own by BiCGStab (van der Vorst 1992; x_0 = 0, shadow residual b, Hermitian
+ * products), (A + c0 I - s_k I) x_k = b until ||r_k|| <= tol ||b||.  All shifts
+ * advance together (each launch covers every active shift) but each has its own
+ * Krylov space: two operator applications per iteration per shift, against one
+ * per iteration for all shifts in msb_multishift_bicg_solve.  b: device vector;
+ * x: device block of n_shifts vectors (output).  HOST outputs (may be NULL):
+ * iters[k], resid[k] (recursive ||r_k|| / ||b||), converged[k].
+ * info->matvecs = 2 * sum_k iters[k]; info->iterations = max_k iters[k].
+ * Allocates four n_shifts x dim work blocks.  Returns MSB_EMAXITER (results
+ * written) if a shift did not converge within maxit or broke down. */
+msb_status msb_bicgstab_solve(msb_op *A, msb_complex c0, const void *b, const msb_complex *shifts, int n_shifts,
+                              double tol, int maxit, msb_precision prec, void *x, int *iters, double *resid,
+                              int *converged, msb_solve_info *info, void *stream);
 
 /* ------------------------------------------------------------------------ */
 /* Second step: batched Lanczos continued fraction (Eq. 1; Sec. III)         */

@@ -63,9 +63,25 @@ def basis_states(L: int, n_up: int, n_dn: int):
         lib.msb_basis_destroy(h)
 
 
+def row_order(L: int, n_dn: int, periodic: bool = True):
+    """Continued-fraction row order: the down-spin state held at each position of a row."""
+    lib = N.load()
+    h = C.c_void_p()
+    N.check(lib.msb_basis_create(L, 0, n_dn, C.byref(h)))
+    try:
+        dd = C.c_int64()
+        N.check(lib.msb_basis_dims(h, None, C.byref(dd), None))
+        order = np.zeros(dd.value, dtype=np.uint16)
+        N.check(lib.msb_basis_row_order(h, 1 if periodic else 0, order.ctypes.data_as(C.POINTER(C.c_uint16))))
+        return order
+    finally:
+        lib.msb_basis_destroy(h)
+
+
 def row_layout(L: int, n_dn: int, periodic: bool = True):
-    """Shared-memory slot of each down-spin state used by the FP32 continued-fraction
-    apply, and the mean worst-bank count per half-warp gather without / with it."""
+    """Shared-memory slot of each row position (in the continued-fraction row order) used
+    by the FP32 continued-fraction apply, and the mean worst-bank count per half-warp
+    gather without / with it."""
     lib = N.load()
     h = C.c_void_p()
     N.check(lib.msb_basis_create(L, 0, n_dn, C.byref(h)))
@@ -175,6 +191,51 @@ class Operator:
             _stream())
         N.check(st, allow=allow_status)
         return x, dict(iters=iters, resid=resid, converged=conv.astype(bool)), info.as_dict(), st
+
+    def bicgstab(self, b: torch.Tensor, shifts, c0: complex = 0.0, tol: float = 1e-10, maxit: int = 20000,
+                 prec: int = FP64, allow_status=(N.MSB_EMAXITER,)):
+        """x_k = (A + c0 - s_k)^{-1} b, each shift by its own BiCGStab (the per-incident-energy
+        baseline).  Returns (x, per-shift dict, info dict, status)."""
+        shifts = np.asarray(shifts, dtype=np.complex128)
+        ns = len(shifts)
+        sh = (N.msb_complex * ns)(*[N.msb_complex(s.real, s.imag) for s in shifts])
+        x = torch.empty((ns, self.dim), dtype=cdtype(prec), device="cuda")
+        iters = np.zeros(ns, dtype=np.int32)
+        resid = np.zeros(ns, dtype=np.float64)
+        conv = np.zeros(ns, dtype=np.int32)
+        info = N.msb_solve_info()
+        c0 = complex(c0)
+        st = N.load().msb_bicgstab_solve(
+            self.h, N.msb_complex(c0.real, c0.imag), _ptr(b.to(cdtype(prec)).contiguous()), sh, ns, tol, maxit, prec,
+            _ptr(x), iters.ctypes.data_as(C.POINTER(C.c_int)), resid.ctypes.data_as(C.POINTER(C.c_double)),
+            conv.ctypes.data_as(C.POINTER(C.c_int)), C.byref(info), _stream())
+        N.check(st, allow=allow_status)
+        return x, dict(iters=iters, resid=resid, converged=conv.astype(bool)), info.as_dict(), st
+
+    def multishift_reseeded(self, b: torch.Tensor, shifts, c0: complex = 0.0, tol: float = 1e-10,
+                            maxit: int = 5000, reseed_tol: float = 1e-8, seed_index: int = 0, max_seeds: int = 8,
+                            block: int = 0, prec: int = FP64):
+        """Adaptive reseeding (App. E): x_k = (A + c0 - s_k)^{-1} b for every shift, reseeded
+        from rejected shifts.  Returns (x, per-shift dict, seeds list, info dict, status)."""
+        shifts = np.asarray(shifts, dtype=np.complex128)
+        ns = len(shifts)
+        sh = (N.msb_complex * ns)(*[N.msb_complex(s.real, s.imag) for s in shifts])
+        x = torch.empty((ns, self.dim), dtype=cdtype(prec), device="cuda")
+        conv = np.zeros(ns, dtype=np.int32)
+        acc = np.zeros(ns, dtype=np.int32)
+        dr = np.zeros(ns, dtype=np.float64)
+        seeds = np.zeros(max_seeds, dtype=np.int32)
+        nseeds = C.c_int()
+        info = N.msb_solve_info()
+        c0 = complex(c0)
+        st = N.load().msb_multishift_bicg_reseeded(
+            self.h, N.msb_complex(c0.real, c0.imag), _ptr(b.to(cdtype(prec)).contiguous()), sh, ns, tol, maxit,
+            block, prec, reseed_tol, seed_index, max_seeds, _ptr(x), conv.ctypes.data_as(C.POINTER(C.c_int)),
+            acc.ctypes.data_as(C.POINTER(C.c_int)), dr.ctypes.data_as(C.POINTER(C.c_double)),
+            seeds.ctypes.data_as(C.POINTER(C.c_int)), C.byref(nseeds), C.byref(info), _stream())
+        N.check(st, allow=(N.MSB_EMAXITER,))
+        per = dict(converged=conv.astype(bool), accepted=acc.astype(bool), dr=dr)
+        return x, per, seeds[:nseeds.value].tolist(), info.as_dict(), st
 
     def continued_fraction(self, phi: torch.Tensor, E0: float, w, eta: float, cf_tol: float = 1e-10,
                            cf_check: int = 50, cf_maxdepth: int = 4000, prec: int | None = None):

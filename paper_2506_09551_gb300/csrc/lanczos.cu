@@ -8,7 +8,6 @@
 // eigenvector is rebuilt by a second, identical pass).
 #include <algorithm>
 #include <cmath>
-#include <mutex>
 #include <string>
 #include <vector>
 
@@ -271,31 +270,42 @@ __global__ void k_scale_real(double* g, int64_t n, double f) {
 // ---------------------------------------------------------------------------
 // Ground state
 // ---------------------------------------------------------------------------
+// Device scratch of one ground-state run: three Lanczos vectors, the start
+// vector of the current restart, H g for the residual check, the coefficients
+// a_k, b_{k+1} (maxit + 1 each), two scalars, the column list and 3 partial
+// sums per block.  Allocated by msb_ground_state, carved from a fixed array by
+// msb_ground_state_noalloc; the Lanczos run below is the same for both.
+struct GroundScratch {
+    double* Q;        // 3 n
+    double* v0;       // n
+    double* hbuf;     // n
+    double* a;        // maxit + 1
+    double* b;        // maxit + 1
+    double* bcur;     // 1
+    double* n0;       // 1
+    int* col0;        // 1
+    double* part;     // 3 * grid
+};
+
 template <class View>
-static void ground_state_impl(const msb_op* op, const View& view, int64_t n, double tol, int maxit, const double* start,
-                              double* g, GroundResult& out, cudaStream_t st) {
+static void lanczos_ground(const msb_op* op, const View& view, int64_t n, double tol, int maxit, const double* start,
+                           double* g, const GroundScratch& S, int grid, GroundResult& out, cudaStream_t st) {
     const double vb = 8.0 * double(n);                       // one real FP64 vector
-    const double hxf = 0.5 * op->hx_flops() + op->matrix_bytes(8) * 0.0;
-    const int grid = grid_for(n, 256, 8);
-    DevBuf<double> Q(3 * size_t(n)), part(size_t(grid) * 3), a_dev(maxit + 1), b_dev(maxit + 1), bcur(1), hbuf(n);
-    DevBuf<int> col0(1);
-    const int zero = 0;
-    col0.upload(&zero, 1, st);
-    DevBuf<double> v0(n);
-    if (start) MSB_CUDA(cudaMemcpyAsync(v0.p, start, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    else { k_fill_start<<<grid, 256, 0, st>>>(v0.p, n, 0x5EEDull); ++out.launches; }
+    const double hxf = 0.5 * op->hx_flops();
+    MSB_CUDA(cudaMemsetAsync(S.col0, 0, sizeof(int), st));
+    if (start) MSB_CUDA(cudaMemcpyAsync(S.v0, start, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    else { k_fill_start<<<grid, 256, 0, st>>>(S.v0, n, 0x5EEDull); ++out.launches; }
     std::vector<double> ha(maxit + 1), hb(maxit + 1), y;
-    DevBuf<double> n0(1);
 
     // One Lanczos run from v0.  If `accumulate`, g = sum_i y[i] q_i.
     auto run = [&](int kmax, bool accumulate, int& k_done) {
-        double* q = Q.p;
-        double* qp = Q.p + n;
-        double* w = Q.p + 2 * n;
-        k_lz_norm_partial<double><<<dim3(grid, 1), 256, 0, st>>>(v0.p, n, col0.p, part.p);
-        k_lz_sum<<<1, 256, 0, st>>>(part.p, grid, col0.p, n0.p, 0, 0);
-        k_lz_start<double><<<dim3(grid, 1), 256, 0, st>>>(v0.p, q, qp, n, col0.p, n0.p);
-        MSB_CUDA(cudaMemsetAsync(bcur.p, 0, sizeof(double), st));
+        double* q = S.Q;
+        double* qp = S.Q + n;
+        double* w = S.Q + 2 * n;
+        k_lz_norm_partial<double><<<dim3(grid, 1), 256, 0, st>>>(S.v0, n, S.col0, S.part);
+        k_lz_sum<<<1, 256, 0, st>>>(S.part, grid, S.col0, S.n0, 0, 0);
+        k_lz_start<double><<<dim3(grid, 1), 256, 0, st>>>(S.v0, q, qp, n, S.col0, S.n0);
+        MSB_CUDA(cudaMemsetAsync(S.bcur, 0, sizeof(double), st));
         out.launches += 3;
         if (accumulate) MSB_CUDA(cudaMemsetAsync(g, 0, n * sizeof(double), st));
         int k = 0;
@@ -304,17 +314,17 @@ static void ground_state_impl(const msb_op* op, const View& view, int64_t n, dou
             if (accumulate && k == kmax - 1) break;
             {
                 ProfScope ps("ground_state", st, 3 * vb + op->matrix_bytes(8), hxf + 4.0 * n);
-                k_lz_apply<View, double><<<dim3(grid, 1), 256, 0, st>>>(view, q, qp, w, n, col0.p, bcur.p, part.p);
+                k_lz_apply<View, double><<<dim3(grid, 1), 256, 0, st>>>(view, q, qp, w, n, S.col0, S.bcur, S.part);
             }
-            { ProfScope ps("ground_state", st, 0, 0); k_lz_sum<<<1, 256, 0, st>>>(part.p, grid, col0.p, a_dev.p, 1, k); }
+            { ProfScope ps("ground_state", st, 0, 0); k_lz_sum<<<1, 256, 0, st>>>(S.part, grid, S.col0, S.a, 1, k); }
             {
                 ProfScope ps("ground_state", st, 3 * vb, 4.0 * n);
-                k_lz_orth<double><<<dim3(grid, 1), 256, 0, st>>>(q, w, n, col0.p, a_dev.p + k, part.p);
+                k_lz_orth<double><<<dim3(grid, 1), 256, 0, st>>>(q, w, n, S.col0, S.a + k, S.part);
             }
-            { ProfScope ps("ground_state", st, 0, 0); k_lz_norm<<<1, 256, 0, st>>>(part.p, grid, col0.p, b_dev.p, 1, k, bcur.p); }
+            { ProfScope ps("ground_state", st, 0, 0); k_lz_norm<<<1, 256, 0, st>>>(S.part, grid, S.col0, S.b, 1, k, S.bcur); }
             {
                 ProfScope ps("ground_state", st, 2 * vb, 1.0 * n);
-                k_lz_scale<double><<<dim3(grid, 1), 256, 0, st>>>(w, n, col0.p, bcur.p);
+                k_lz_scale<double><<<dim3(grid, 1), 256, 0, st>>>(w, n, S.col0, S.bcur);
             }
             out.launches += 5;
             ++out.matvecs;
@@ -322,8 +332,8 @@ static void ground_state_impl(const msb_op* op, const View& view, int64_t n, dou
             std::swap(qp, q);   // q_prev <- q
             std::swap(q, w);    // q <- w (scaled), w <- old q_prev
             if (!accumulate) {
-                MSB_CUDA(cudaMemcpyAsync(ha.data(), a_dev.p, (k + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
-                MSB_CUDA(cudaMemcpyAsync(hb.data(), b_dev.p, (k + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
+                MSB_CUDA(cudaMemcpyAsync(ha.data(), S.a, (k + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
+                MSB_CUDA(cudaMemcpyAsync(hb.data(), S.b, (k + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
                 MSB_CUDA(cudaStreamSynchronize(st));
                 double theta;
                 tridiag_lowest(ha, hb, k + 1, theta, y);
@@ -340,25 +350,25 @@ static void ground_state_impl(const msb_op* op, const View& view, int64_t n, dou
     out.status = MSB_OK;
     for (int restart = 0; restart < 20; ++restart) {
         int K = 0;
-        run(std::min<int64_t>(maxit, n), false, K);
+        run(int(std::min<int64_t>(maxit, n)), false, K);
         double theta;
         tridiag_lowest(ha, hb, K, theta, y);
         int K2 = 0;
         run(K, true, K2);
         // E = <g|Hg>/<g|g>, residual ||Hg - E g|| / ||g||
-        k_gs_check<View><<<grid, 256, 0, st>>>(view, g, hbuf.p, n, part.p);
+        k_gs_check<View><<<grid, 256, 0, st>>>(view, g, S.hbuf, n, S.part);
         std::vector<double> hp(size_t(grid) * 3);
-        MSB_CUDA(cudaMemcpyAsync(hp.data(), part.p, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+        MSB_CUDA(cudaMemcpyAsync(hp.data(), S.part, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
         MSB_CUDA(cudaStreamSynchronize(st));
         double gh = 0, hh = 0, gg = 0;
         for (int b = 0; b < grid; ++b) { gh += hp[3 * b]; hh += hp[3 * b + 1]; gg += hp[3 * b + 2]; }
         const double nrm = std::sqrt(gg);
         k_scale_real<<<grid, 256, 0, st>>>(g, n, 1.0 / nrm);
-        k_scale_real<<<grid, 256, 0, st>>>(hbuf.p, n, 1.0 / nrm);
+        k_scale_real<<<grid, 256, 0, st>>>(S.hbuf, n, 1.0 / nrm);
         const double E = gh / gg;
-        k_gs_resid_partial<<<grid, 256, 0, st>>>(g, hbuf.p, n, E, part.p);
+        k_gs_resid_partial<<<grid, 256, 0, st>>>(g, S.hbuf, n, E, S.part);
         std::vector<double> rp(grid);
-        MSB_CUDA(cudaMemcpyAsync(rp.data(), part.p, grid * sizeof(double), cudaMemcpyDeviceToHost, st));
+        MSB_CUDA(cudaMemcpyAsync(rp.data(), S.part, grid * sizeof(double), cudaMemcpyDeviceToHost, st));
         MSB_CUDA(cudaStreamSynchronize(st));
         double rr = 0;
         for (double v : rp) rr += v;
@@ -368,9 +378,20 @@ static void ground_state_impl(const msb_op* op, const View& view, int64_t n, dou
         out.residual = std::sqrt(rr);
         out.restarts = restart;
         if (out.residual <= tol * std::max(1.0, std::fabs(E))) return;
-        MSB_CUDA(cudaMemcpyAsync(v0.p, g, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        MSB_CUDA(cudaMemcpyAsync(S.v0, g, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
     }
     out.status = MSB_EMAXITER;
+}
+
+template <class View>
+static void ground_state_impl(const msb_op* op, const View& view, int64_t n, double tol, int maxit, const double* start,
+                              double* g, GroundResult& out, cudaStream_t st) {
+    const int grid = grid_for(n, 256, 8);
+    DevBuf<double> Q(3 * size_t(n)), v0(n), hbuf(n), part(size_t(grid) * 3), a_dev(maxit + 1), b_dev(maxit + 1),
+        bcur(1), n0(1);
+    DevBuf<int> col0(1);
+    const GroundScratch S{Q.p, v0.p, hbuf.p, a_dev.p, b_dev.p, bcur.p, n0.p, col0.p, part.p};
+    lanczos_ground(op, view, n, tol, maxit, start, g, S, grid, out, st);
 }
 
 void ground_state(msb_op* H, double tol, int maxit, const double* start, double* g, GroundResult& out,
@@ -559,11 +580,11 @@ __global__ void __launch_bounds__(256, 6) k_cf_apply_hub(HubView h0, const HubVi
             ay = fma(s_usg[e], v.y, ay);
         }
         // down-spin hops: table entries, then row values, four at a time
-        const int nd = __ldg(h.ndn + d);
+        const int nd = __ldg(h.ndnp + d);
         e = 0;
         for (; e + 4 <= nd; e += 4) {
-            const int32_t h0 = __ldg(h.hdn + e * Ddn + d), h1 = __ldg(h.hdn + (e + 1) * Ddn + d);
-            const int32_t h2 = __ldg(h.hdn + (e + 2) * Ddn + d), h3 = __ldg(h.hdn + (e + 3) * Ddn + d);
+            const int h0 = __ldg(h.hdn16 + e * Ddn + d), h1 = __ldg(h.hdn16 + (e + 1) * Ddn + d);
+            const int h2 = __ldg(h.hdn16 + (e + 2) * Ddn + d), h3 = __ldg(h.hdn16 + (e + 3) * Ddn + d);
             const C v0 = row[h0 >> 1], v1 = row[h1 >> 1], v2 = row[h2 >> 1], v3 = row[h3 >> 1];
             const S g0 = (h0 & 1) ? S(-1) : S(1), g1 = (h1 & 1) ? S(-1) : S(1);
             const S g2 = (h2 & 1) ? S(-1) : S(1), g3 = (h3 & 1) ? S(-1) : S(1);
@@ -577,13 +598,13 @@ __global__ void __launch_bounds__(256, 6) k_cf_apply_hub(HubView h0, const HubVi
             ay = fma(g3, v3.y, ay);
         }
         for (; e < nd; ++e) {
-            const int32_t hh = __ldg(h.hdn + e * Ddn + d);
+            const int hh = __ldg(h.hdn16 + e * Ddn + d);
             const C v = row[hh >> 1];
             const S sg = (hh & 1) ? S(-1) : S(1);
             ax = fma(sg, v.x, ax);
             ay = fma(sg, v.y, ay);
         }
-        const uint32_t sd = __ldg(h.sdn + d);
+        const uint32_t sd = __ldg(h.sdnp + d);
         const int nb = core >= 0 ? ubits + int((sd >> core) & 1u) : 0;
         const S dg = lut[__popc(su & sd) + nb * (L + 1)];
         const C x = row[d];
@@ -646,7 +667,7 @@ __device__ __forceinline__ long long fx_term(double v, int eB, long long neg) {
 __device__ __forceinline__ long long fx_signed(long long f, long long neg) { return (f ^ neg) - neg; }
 
 
-template <bool Multi>
+template <bool Multi, bool Signed>
 __global__ void __launch_bounds__(256, 5) k_cf_apply_hub_fx(HubView h0, const HubView* __restrict__ hv,
                                                             const int* __restrict__ colq,
                                                             const double2* __restrict__ Vk,
@@ -691,7 +712,7 @@ __global__ void __launch_bounds__(256, 5) k_cf_apply_hub_fx(HubView h0, const Hu
     if (threadIdx.x < nu) {
         const int32_t ent = __ldg(h.hup + int64_t(threadIdx.x) * h.Dup + u);
         s_uoff[threadIdx.x] = (ent >> 1) * Ddn;
-        s_uneg[threadIdx.x] = -(ent & 1);
+        s_uneg[threadIdx.x] = Signed ? -(ent & 1) : 0;
     }
     __syncthreads();
     const int core = h.core;
@@ -699,7 +720,7 @@ __global__ void __launch_bounds__(256, 5) k_cf_apply_hub_fx(HubView h0, const Hu
     // -t sig times the fixed-point unit 2^(eB - 1080) (an exact power of two)
     const double mts = (-h.t * sig) * __longlong_as_double(static_cast<long long>(eB - 57) << 52);
     const double mcB = -cB;
-    const uint16_t* __restrict__ t16 = h.hdn16;                     // [slot][state], (target << 1) | neg
+    const uint16_t* __restrict__ t16 = h.hdn16;                     // [slot][position], (target << 1) | neg
     double dot = 0.0;
     // Every lane of a warp runs the same iterations (lanes past the row idle,
     // guarded), so the down-spin loop runs to a warp-uniform count.
@@ -713,7 +734,8 @@ __global__ void __launch_bounds__(256, 5) k_cf_apply_hub_fx(HubView h0, const Hu
         for (; e + 4 <= nu; e += 4) {
             const double2 v0 = Vc[s_uoff[e] + d], v1 = Vc[s_uoff[e + 1] + d];
             const double2 v2 = Vc[s_uoff[e + 2] + d], v3 = Vc[s_uoff[e + 3] + d];
-            const long long g0 = s_uneg[e], g1 = s_uneg[e + 1], g2 = s_uneg[e + 2], g3 = s_uneg[e + 3];
+            const long long g0 = Signed ? s_uneg[e] : 0, g1 = Signed ? s_uneg[e + 1] : 0;
+            const long long g2 = Signed ? s_uneg[e + 2] : 0, g3 = Signed ? s_uneg[e + 3] : 0;
             ax += fx_term(v0.x, eB, g0);
             ay += fx_term(v0.y, eB, g0);
             ax += fx_term(v1.x, eB, g1);
@@ -725,18 +747,19 @@ __global__ void __launch_bounds__(256, 5) k_cf_apply_hub_fx(HubView h0, const Hu
         }
         for (; e < nu; ++e) {
             const double2 v = Vc[s_uoff[e] + d];
-            const long long g = s_uneg[e];
+            const long long g = Signed ? s_uneg[e] : 0;
             ax += fx_term(v.x, eB, g);
             ay += fx_term(v.y, eB, g);
         }
         // slots past an element's own count hold the zero slot: no per-hop predicate
-        const int nd = __reduce_max_sync(0xffffffffu, act ? int(__ldg(h.ndn + d)) : 0);
+        const int nd = __reduce_max_sync(0xffffffffu, act ? int(__ldg(h.ndnp + d)) : 0);
         e = 0;
         for (; e + 4 <= nd; e += 4) {
             const int h0 = __ldg(t16 + e * Ddn + d), h1 = __ldg(t16 + (e + 1) * Ddn + d);
             const int h2 = __ldg(t16 + (e + 2) * Ddn + d), h3 = __ldg(t16 + (e + 3) * Ddn + d);
             const longlong2 f0 = row[h0 >> 1], f1 = row[h1 >> 1], f2 = row[h2 >> 1], f3 = row[h3 >> 1];
-            const long long g0 = -(h0 & 1), g1 = -(h1 & 1), g2 = -(h2 & 1), g3 = -(h3 & 1);
+            const long long g0 = Signed ? -(h0 & 1) : 0, g1 = Signed ? -(h1 & 1) : 0;
+            const long long g2 = Signed ? -(h2 & 1) : 0, g3 = Signed ? -(h3 & 1) : 0;
             ax += fx_signed(f0.x, g0);
             ay += fx_signed(f0.y, g0);
             ax += fx_signed(f1.x, g1);
@@ -749,11 +772,11 @@ __global__ void __launch_bounds__(256, 5) k_cf_apply_hub_fx(HubView h0, const Hu
         for (; e < nd; ++e) {
             const int hh = __ldg(t16 + e * Ddn + d);
             const longlong2 f = row[hh >> 1];
-            const long long g = -(hh & 1);
+            const long long g = Signed ? -(hh & 1) : 0;
             ax += fx_signed(f.x, g);
             ay += fx_signed(f.y, g);
         }
-        const uint32_t sd = __ldg(h.sdn + d);
+        const uint32_t sd = __ldg(h.sdnp + d);
         const int nb = core >= 0 ? ubits + int((sd >> core) & 1u) : 0;
         const double dg = lut[__popc(su & sd) + nb * (L + 1)];
         if (!act) continue;                                      // warp-uniform part done
@@ -783,7 +806,7 @@ __global__ void __launch_bounds__(256, 5) k_cf_apply_hub_fx(HubView h0, const Hu
 // largest hop count, empty slots reading the zero kept past the row.  No FP64
 // instruction: coefficients arrive as FP32 copies, the product is compensated
 // FP32, and the block sum is float-float.
-template <bool Multi>
+template <bool Multi, bool Signed>
 __global__ void __launch_bounds__(256, 6) k_cf_apply_hub_f2x2(HubView h0, const HubView* __restrict__ hv,
                                                               const int* __restrict__ colq,
                                                               const float2* __restrict__ Vk,
@@ -842,7 +865,7 @@ __global__ void __launch_bounds__(256, 6) k_cf_apply_hub_f2x2(HubView h0, const 
     if (threadIdx.x < nu) {
         const int32_t ent = __ldg(h.hup + int64_t(threadIdx.x) * h.Dup + u);
         s_uoff[threadIdx.x] = ((ent >> 1) * Ddn) >> 1;           // in float4 units
-        s_usg[threadIdx.x] = (ent & 1) ? -1.f : 1.f;
+        s_usg[threadIdx.x] = (Signed && (ent & 1)) ? -1.f : 1.f;
     }
     __syncthreads();
     const int core = h.core;
@@ -851,8 +874,8 @@ __global__ void __launch_bounds__(256, 6) k_cf_apply_hub_f2x2(HubView h0, const 
     const float mcB = -cB;
     const float4* __restrict__ Vc4 = reinterpret_cast<const float4*>(Vc);
     const uint32_t* __restrict__ t32 = reinterpret_cast<const uint32_t*>(placed ? h.hdn16p : h.hdn16);
-    const uint16_t* __restrict__ n16 = reinterpret_cast<const uint16_t*>(h.ndn);
-    const uint2* __restrict__ sd2 = reinterpret_cast<const uint2*>(h.sdn);
+    const uint16_t* __restrict__ n16 = reinterpret_cast<const uint16_t*>(h.ndnp);
+    const uint2* __restrict__ sd2 = reinterpret_cast<const uint2*>(h.sdnp);
     float dhi = 0.f, dlo = 0.f;
     // Every lane of a warp runs the same iterations (lanes past the row idle, guarded),
     // so the down-spin loop can use a warp-uniform trip count without divergence.
@@ -866,15 +889,20 @@ __global__ void __launch_bounds__(256, 6) k_cf_apply_hub_f2x2(HubView h0, const 
         int e = 0;
         for (; e + 2 <= nu; e += 2) {
             const float4 v = Vc4[s_uoff[e] + q], w4 = Vc4[s_uoff[e + 1] + q];
-            const float g = s_usg[e], g2 = s_usg[e + 1];
-            a0x = fmaf(g, v.x, a0x); a0y = fmaf(g, v.y, a0y);
-            a1x = fmaf(g, v.z, a1x); a1y = fmaf(g, v.w, a1y);
-            a0x = fmaf(g2, w4.x, a0x); a0y = fmaf(g2, w4.y, a0y);
-            a1x = fmaf(g2, w4.z, a1x); a1y = fmaf(g2, w4.w, a1y);
+            if constexpr (Signed) {
+                const float g = s_usg[e], g2 = s_usg[e + 1];
+                a0x = fmaf(g, v.x, a0x); a0y = fmaf(g, v.y, a0y);
+                a1x = fmaf(g, v.z, a1x); a1y = fmaf(g, v.w, a1y);
+                a0x = fmaf(g2, w4.x, a0x); a0y = fmaf(g2, w4.y, a0y);
+                a1x = fmaf(g2, w4.z, a1x); a1y = fmaf(g2, w4.w, a1y);
+            } else {
+                a0x += v.x + w4.x; a0y += v.y + w4.y;
+                a1x += v.z + w4.z; a1y += v.w + w4.w;
+            }
         }
         if (e < nu) {
             const float4 v = Vc4[s_uoff[e] + q];
-            const float g = s_usg[e];
+            const float g = Signed ? s_usg[e] : 1.f;
             a0x = fmaf(g, v.x, a0x); a0y = fmaf(g, v.y, a0y);
             a1x = fmaf(g, v.z, a1x); a1y = fmaf(g, v.w, a1y);
         }
@@ -886,9 +914,14 @@ __global__ void __launch_bounds__(256, 6) k_cf_apply_hub_f2x2(HubView h0, const 
         for (int k = 0; k < ndw; ++k, tp += step) {
             const uint32_t ta = __ldg(tp);                      // one hop of each element
             const float2 va = row[(ta & 0xFFFFu) >> 1], vb = row[ta >> 17];
-            const float ga = (ta & 1u) ? -1.f : 1.f, gb = (ta & 0x10000u) ? -1.f : 1.f;
-            a0x = fmaf(ga, va.x, a0x); a0y = fmaf(ga, va.y, a0y);
-            a1x = fmaf(gb, vb.x, a1x); a1y = fmaf(gb, vb.y, a1y);
+            if constexpr (Signed) {
+                const float ga = (ta & 1u) ? -1.f : 1.f, gb = (ta & 0x10000u) ? -1.f : 1.f;
+                a0x = fmaf(ga, va.x, a0x); a0y = fmaf(ga, va.y, a0y);
+                a1x = fmaf(gb, vb.x, a1x); a1y = fmaf(gb, vb.y, a1y);
+            } else {
+                a0x += va.x; a0y += va.y;
+                a1x += vb.x; a1y += vb.y;
+            }
         }
         const uint2 sd = __ldg(sd2 + q);
         const int nb0 = core >= 0 ? ubits + int((sd.x >> core) & 1u) : 0;
@@ -1054,20 +1087,32 @@ __global__ void k_cf_reduce_b(const double* part, int nblk, const int* cols, dou
 
 // V_0 = phi (copied: the input is not modified; padding zeroed); the other two
 // vector blocks get a zero padding; partial ||phi||^2.  Column c of phi starts
-// at c * ldphi and has nlen[c] elements.
+// at c * ldphi and has nlen[c] elements.  With the row-tiled Hubbard apply
+// (hv != null) the column is stored in the continued-fraction row order of its
+// operator: element (u, p) of V_0 is phi's element (u, dpos[p]).
 template <typename C>
 __global__ void __launch_bounds__(256) k_cf_start(const C* __restrict__ phi, int64_t ldphi,
-                                                  const int64_t* __restrict__ nlen, C* __restrict__ V0,
+                                                  const int64_t* __restrict__ nlen, const HubView* __restrict__ hv,
+                                                  const int* __restrict__ colq, C* __restrict__ V0,
                                                   C* __restrict__ V1, C* __restrict__ V2, int64_t ld, double* part) {
     using S = scalar_t<C>;
     __shared__ double sm[32];
     const int c = blockIdx.y;
     const int64_t n = nlen[c];
+    const uint16_t* __restrict__ dpos = hv ? hv[colq[c]].dpos : nullptr;
+    const int64_t Ddn = hv ? hv[colq[c]].Ddn : 1;
     double acc = 0.0;
     float hi = 0.f, lo = 0.f;
     for (int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < ld; s += int64_t(gridDim.x) * blockDim.x) {
         C x = mk(S(0), S(0));
-        if (s < n) x = phi[int64_t(c) * ldphi + s];
+        if (s < n) {
+            int64_t src = s;
+            if (dpos) {
+                const int64_t u = s / Ddn;
+                src = u * Ddn + __ldg(dpos + (s - u * Ddn));
+            }
+            x = phi[int64_t(c) * ldphi + src];
+        }
         V0[int64_t(c) * ld + s] = x;
         if (s >= n) {
             V1[int64_t(c) * ld + s] = x;
@@ -1119,7 +1164,7 @@ static void cf_impl(const CFColumns& P, const View& view, const double* w, int n
     const int per = int(16 / sizeof(C));
     const int grid = grid_for(ld / per, 256, 4);
     int64_t hub_smem = 0;
-    bool rows = false, pair = false, fx = false;
+    bool rows = false, pair = false, fx = false, sgn = false;
     int fx_threads = 256;
     int nblkA = grid;
     std::vector<HubView> hviews;
@@ -1135,9 +1180,9 @@ static void cf_impl(const CFColumns& P, const View& view, const double* w, int n
             maxDdn = std::max(maxDdn, h.Ddn);
             maxDup = std::max(maxDup, h.Dup);
             maxL = std::max(maxL, h.L);
-            rows = rows && h.Wup <= kMaxHops && h.Dup * h.Ddn < (int64_t(1) << 31);
-            pair = pair && h.Ddn % 2 == 0 && h.hdn16 != nullptr;
-            fx = fx && h.hdn16 != nullptr;
+            rows = rows && h.Wup <= kMaxHops && h.Dup * h.Ddn < (int64_t(1) << 31) && h.hdn16 != nullptr;
+            pair = pair && h.Ddn % 2 == 0;
+            sgn = sgn || h.usign || h.dsign;
         }
         hub_smem = (maxDdn + 2) * int64_t(sizeof(C)) + 3 * (maxL + 1) * 8;   // row, two zero slots, table
         rows = rows && hub_smem <= 160 * 1024;
@@ -1146,14 +1191,17 @@ static void cf_impl(const CFColumns& P, const View& view, const double* w, int n
         // are paid over twice the work); longer rows keep 256 threads, where shared
         // memory, not registers, limits the CTAs per SM.
         fx_threads = maxDdn <= 1024 ? 128 : 256;
-        if (std::is_same<C, double2>::value && !fx) rows = false;   // FP64 rows need the 16-bit table
+        fx = fx && rows;
+        pair = pair && rows;
         if (rows) {
             nblkA = int(maxDup);
             const void* fn = nullptr;
             if (fx)
-                fn = multi ? (const void*)k_cf_apply_hub_fx<true> : (const void*)k_cf_apply_hub_fx<false>;
+                fn = multi ? (sgn ? (const void*)k_cf_apply_hub_fx<true, true> : (const void*)k_cf_apply_hub_fx<true, false>)
+                           : (sgn ? (const void*)k_cf_apply_hub_fx<false, true> : (const void*)k_cf_apply_hub_fx<false, false>);
             else if (pair)
-                fn = multi ? (const void*)k_cf_apply_hub_f2x2<true> : (const void*)k_cf_apply_hub_f2x2<false>;
+                fn = multi ? (sgn ? (const void*)k_cf_apply_hub_f2x2<true, true> : (const void*)k_cf_apply_hub_f2x2<true, false>)
+                           : (sgn ? (const void*)k_cf_apply_hub_f2x2<false, true> : (const void*)k_cf_apply_hub_f2x2<false, false>);
             else
                 fn = multi ? (const void*)k_cf_apply_hub<float2, true> : (const void*)k_cf_apply_hub<float2, false>;
             MSB_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(hub_smem)));
@@ -1185,7 +1233,8 @@ static void cf_impl(const CFColumns& P, const View& view, const double* w, int n
     for (int c = 0; c < nv; ++c) all_elems += double(nlen[c]);
     {
         ProfScope ps("cf_start", st, 2.0 * all_elems * sizeof(C), 4.0 * all_elems);
-        k_cf_start<C><<<dim3(grid, nv), 256, 0, st>>>(phi, P.ldphi, nlen_d.p, vk, vkm1, wv, ld, part.p);
+        k_cf_start<C><<<dim3(grid, nv), 256, 0, st>>>(phi, P.ldphi, nlen_d.p, rows ? hv.p : nullptr, colq.p, vk, vkm1,
+                                                       wv, ld, part.p);
     }
     { ProfScope ps("cf_reduce", st, 0, 0); k_cf_setup<<<nv, 256, 0, st>>>(part.p, grid, n0.p, cf); }
     out.launches += 2;
@@ -1222,23 +1271,17 @@ static void cf_impl(const CFColumns& P, const View& view, const double* w, int n
                     auto x = reinterpret_cast<const double2*>(vk);
                     auto xm = reinterpret_cast<const double2*>(vkm1);
                     auto y = reinterpret_cast<double2*>(wv);
-                    if (multi)
-                        k_cf_apply_hub_fx<true><<<g, fx_threads, hub_smem, st>>>(view, hv.p, colq.p, x, xm, y, ld, cols.p,
-                                                                          cf, part.p);
-                    else
-                        k_cf_apply_hub_fx<false><<<g, fx_threads, hub_smem, st>>>(view, hv.p, colq.p, x, xm, y, ld,
-                                                                           cols.p, cf, part.p);
+                    auto kern = multi ? (sgn ? k_cf_apply_hub_fx<true, true> : k_cf_apply_hub_fx<true, false>)
+                                      : (sgn ? k_cf_apply_hub_fx<false, true> : k_cf_apply_hub_fx<false, false>);
+                    kern<<<g, fx_threads, hub_smem, st>>>(view, hv.p, colq.p, x, xm, y, ld, cols.p, cf, part.p);
                     done_hub = true;
                 } else if (rows && pair) {
                     auto x = reinterpret_cast<const float2*>(vk);
                     auto xm = reinterpret_cast<const float2*>(vkm1);
                     auto y = reinterpret_cast<float2*>(wv);
-                    if (multi)
-                        k_cf_apply_hub_f2x2<true><<<g, kApplyThreads, hub_smem, st>>>(view, hv.p, colq.p, x, xm, y, ld,
-                                                                            cols.p, cf, part.p);
-                    else
-                        k_cf_apply_hub_f2x2<false><<<g, kApplyThreads, hub_smem, st>>>(view, hv.p, colq.p, x, xm, y, ld,
-                                                                             cols.p, cf, part.p);
+                    auto kern = multi ? (sgn ? k_cf_apply_hub_f2x2<true, true> : k_cf_apply_hub_f2x2<true, false>)
+                                      : (sgn ? k_cf_apply_hub_f2x2<false, true> : k_cf_apply_hub_f2x2<false, false>);
+                    kern<<<g, kApplyThreads, hub_smem, st>>>(view, hv.p, colq.p, x, xm, y, ld, cols.p, cf, part.p);
                     done_hub = true;
                 } else if (rows) {
                     // FP32 with an odd D_dn (FP64 always takes the fixed-point kernel)
@@ -1393,18 +1436,18 @@ extern "C" msb_status msb_continued_fraction(msb_op* H, const void* phi, int n_v
 // ---------------------------------------------------------------------------
 // Ground state without any device allocation.
 //
-// Some callers cannot call cudaMalloc: code that runs while a stream is being
-// captured in global capture mode (allocation is not a capturable operation
-// and is refused there), and hosts whose device memory is owned by another
-// allocator under a fixed budget.  For them, msb_ground_state_noalloc runs the
-// same Lanczos kernels as msb_ground_state on a fixed scratch array that lives
-// in the library image: every GPU that loads the library holds it until the
-// process exits.  Its device address is looked up once per device (the first
-// call on a device does this set-up, so that first call should come before
-// any stream capture begins).  All calls share the array and it keeps the
-// previous call's contents; every part the Lanczos run reads is written first
-// in the call.  Calls that overlap on the GPU (two streams, or two threads)
-// race on the array.
+// Some callers cannot call cudaMalloc: a host process whose device memory is
+// owned by another allocator under a fixed budget (a framework's caching pool,
+// a serving process that reserved all memory at start-up), where an extra
+// allocation fails or fragments that budget.  For them,
+// msb_ground_state_noalloc runs the same Lanczos run as msb_ground_state
+// (lanczos_ground above) on a fixed scratch array that lives in the library
+// image: every GPU that loads the library holds it until the process exits.
+// Its device address is looked up at the start of every call, with the
+// caller's current device, so it stays valid after a cudaDeviceReset.  All
+// calls share the array and it keeps the previous call's contents; every part
+// the Lanczos run reads is written first in the call.  Calls that overlap on
+// the GPU (two streams, or two threads) race on the array.
 // ---------------------------------------------------------------------------
 namespace msb {
 
@@ -1417,117 +1460,32 @@ constexpr int64_t kNoAllocDoubles =
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
 
 static double* noalloc_scratch_address() {
-    static std::mutex mu;
-    static double* addr[64] = {nullptr};
-    int dev = 0;
-    MSB_CUDA(cudaGetDevice(&dev));
-    MSB_REQUIRE(dev >= 0 && dev < 64, "device index out of range");
-    std::lock_guard<std::mutex> lk(mu);
-    if (!addr[dev]) {
-        void* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            fail(MSB_ECUDA, std::string("cudaGetSymbolAddress of the no-alloc scratch: ") + cudaGetErrorString(e));
-        }
-        addr[dev] = static_cast<double*>(p);
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        fail(MSB_ECUDA, std::string("cudaGetSymbolAddress of the no-alloc scratch: ") + cudaGetErrorString(e));
     }
-    return addr[dev];
+    return static_cast<double*>(p);
 }
 
 template <class View>
-static void ground_state_noalloc_impl(const View& view, int64_t n, double tol, int maxit, const double* start,
-                                      double* g, GroundResult& out, cudaStream_t st) {
+static void ground_state_noalloc_impl(const msb_op* op, const View& view, int64_t n, double tol, int maxit,
+                                      const double* start, double* g, GroundResult& out, cudaStream_t st) {
     const int grid = grid_for(n, 256, 8);
     MSB_REQUIRE(grid <= kNoAllocMaxGrid, "grid exceeds the no-alloc scratch layout");
     double* base = noalloc_scratch_address();
-    double* Q = base;                         // 3 Lanczos vectors
-    double* v0 = base + 3 * n;                // start vector of the current restart
-    double* hbuf = base + 4 * n;              // H g for the residual check
-    double* a_dev = base + 5 * n;             // a_k
-    double* b_dev = a_dev + (maxit + 1);      // b_{k+1}
-    double* bcur = b_dev + (maxit + 1);
-    double* n0 = bcur + 1;
-    int* col0 = reinterpret_cast<int*>(n0 + 1);
-    double* part = n0 + 2;                    // partial sums, 3 per block
-    MSB_CUDA(cudaMemsetAsync(col0, 0, sizeof(int), st));
-    if (start) MSB_CUDA(cudaMemcpyAsync(v0, start, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    else { k_fill_start<<<grid, 256, 0, st>>>(v0, n, 0x5EEDull); ++out.launches; }
-    std::vector<double> ha(maxit + 1), hb(maxit + 1), y;
-
-    auto run = [&](int kmax, bool accumulate, int& k_done) {
-        double* q = Q;
-        double* qp = Q + n;
-        double* w = Q + 2 * n;
-        k_lz_norm_partial<double><<<dim3(grid, 1), 256, 0, st>>>(v0, n, col0, part);
-        k_lz_sum<<<1, 256, 0, st>>>(part, grid, col0, n0, 0, 0);
-        k_lz_start<double><<<dim3(grid, 1), 256, 0, st>>>(v0, q, qp, n, col0, n0);
-        MSB_CUDA(cudaMemsetAsync(bcur, 0, sizeof(double), st));
-        out.launches += 3;
-        if (accumulate) MSB_CUDA(cudaMemsetAsync(g, 0, n * sizeof(double), st));
-        int k = 0;
-        for (; k < kmax; ++k) {
-            if (accumulate) { k_axpy_real<<<grid, 256, 0, st>>>(g, q, n, y[k]); ++out.launches; }
-            if (accumulate && k == kmax - 1) break;
-            k_lz_apply<View, double><<<dim3(grid, 1), 256, 0, st>>>(view, q, qp, w, n, col0, bcur, part);
-            k_lz_sum<<<1, 256, 0, st>>>(part, grid, col0, a_dev, 1, k);
-            k_lz_orth<double><<<dim3(grid, 1), 256, 0, st>>>(q, w, n, col0, a_dev + k, part);
-            k_lz_norm<<<1, 256, 0, st>>>(part, grid, col0, b_dev, 1, k, bcur);
-            k_lz_scale<double><<<dim3(grid, 1), 256, 0, st>>>(w, n, col0, bcur);
-            out.launches += 5;
-            ++out.matvecs;
-            MSB_LAUNCH_CHECK();
-            std::swap(qp, q);
-            std::swap(q, w);
-            if (!accumulate) {
-                MSB_CUDA(cudaMemcpyAsync(ha.data(), a_dev, (k + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
-                MSB_CUDA(cudaMemcpyAsync(hb.data(), b_dev, (k + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
-                MSB_CUDA(cudaStreamSynchronize(st));
-                double theta;
-                tridiag_lowest(ha, hb, k + 1, theta, y);
-                const double est = std::fabs(hb[k] * y[k]);
-                if (est <= 0.01 * tol * std::max(1.0, std::fabs(theta)) || hb[k] <= 1e-300 || k + 1 >= n) {
-                    ++k;
-                    break;
-                }
-            }
-        }
-        k_done = accumulate ? kmax : k;
-    };
-
-    out.status = MSB_OK;
-    for (int restart = 0; restart < 20; ++restart) {
-        int K = 0;
-        run(int(std::min<int64_t>(maxit, n)), false, K);
-        double theta;
-        tridiag_lowest(ha, hb, K, theta, y);
-        int K2 = 0;
-        run(K, true, K2);
-        k_gs_check<View><<<grid, 256, 0, st>>>(view, g, hbuf, n, part);
-        std::vector<double> hp(size_t(grid) * 3);
-        MSB_CUDA(cudaMemcpyAsync(hp.data(), part, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
-        MSB_CUDA(cudaStreamSynchronize(st));
-        double gh = 0, hh = 0, gg = 0;
-        for (int b = 0; b < grid; ++b) { gh += hp[3 * b]; hh += hp[3 * b + 1]; gg += hp[3 * b + 2]; }
-        const double nrm = std::sqrt(gg);
-        k_scale_real<<<grid, 256, 0, st>>>(g, n, 1.0 / nrm);
-        k_scale_real<<<grid, 256, 0, st>>>(hbuf, n, 1.0 / nrm);
-        const double E = gh / gg;
-        k_gs_resid_partial<<<grid, 256, 0, st>>>(g, hbuf, n, E, part);
-        std::vector<double> rp(grid);
-        MSB_CUDA(cudaMemcpyAsync(rp.data(), part, grid * sizeof(double), cudaMemcpyDeviceToHost, st));
-        MSB_CUDA(cudaStreamSynchronize(st));
-        double rr = 0;
-        for (double v : rp) rr += v;
-        out.launches += 4;
-        ++out.matvecs;
-        out.E = E;
-        out.residual = std::sqrt(rr);
-        out.restarts = restart;
-        if (out.residual <= tol * std::max(1.0, std::fabs(E))) return;
-        MSB_CUDA(cudaMemcpyAsync(v0, g, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    }
-    out.status = MSB_EMAXITER;
+    GroundScratch S;
+    S.Q = base;                               // 3 Lanczos vectors
+    S.v0 = base + 3 * n;                      // start vector of the current restart
+    S.hbuf = base + 4 * n;                    // H g for the residual check
+    S.a = base + 5 * n;                       // a_k
+    S.b = S.a + (maxit + 1);                  // b_{k+1}
+    S.bcur = S.b + (maxit + 1);
+    S.n0 = S.bcur + 1;
+    S.col0 = reinterpret_cast<int*>(S.n0 + 1);
+    S.part = S.n0 + 2;                        // partial sums, 3 per block
+    lanczos_ground(op, view, n, tol, maxit, start, g, S, grid, out, st);
 }
 
 }  // namespace msb
@@ -1550,8 +1508,8 @@ extern "C" msb_status msb_ground_state_noalloc(msb_op* H, double tol, int maxit,
         MSB_REQUIRE(H->kind != 2, "a direct sum has no single ground state: take each part's");
         cudaStream_t st = (cudaStream_t)stream;
         msb::GroundResult r;
-        if (H->kind == 0) msb::ground_state_noalloc_impl(H->hub, H->dim, tol, maxit, start, g, r, st);
-        else msb::ground_state_noalloc_impl(H->csr, H->dim, tol, maxit, start, g, r, st);
+        if (H->kind == 0) msb::ground_state_noalloc_impl(H, H->hub, H->dim, tol, maxit, start, g, r, st);
+        else msb::ground_state_noalloc_impl(H, H->csr, H->dim, tol, maxit, start, g, r, st);
         MSB_CUDA(cudaStreamSynchronize(st));
         if (E_G) *E_G = r.E;
         if (residual) *residual = r.residual;

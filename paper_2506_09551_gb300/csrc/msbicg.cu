@@ -200,11 +200,15 @@ __global__ void __launch_bounds__(256) k_seed_update(V* ring, const V* __restric
 }
 
 // beta, convergence of every shift, iteration bookkeeping, seed rescaling.
+// The rescale 2^f of r~_{m+1} is committed only if the solve goes on (a finished
+// solve keeps r~ as it is), so that fz_coef, the factor from the stored r~_{m+1}
+// to each tested shift's recursive residual, matches what the ring holds.
 __global__ void __launch_bounds__(kScalarThreads) k_scalar_b(SeedState* st, const double* part, int nblk,
                                                              ShiftArrays sh, int ns, int nslot) {
     if (st->done) return;
     __shared__ double sm[3 * 32];
     __shared__ double s_rn;      // ||r~_{m+1}|| (stored scale S_m)
+    __shared__ double2 s_rho;    // (r~_{m+1}, r~_{m+1}) at scale S_m
     __shared__ int s_m, s_stop, s_f;
     double v[3];
     reduce_partials<3>(part, nblk, v, sm);
@@ -229,11 +233,9 @@ __global__ void __launch_bounds__(kScalarThreads) k_scalar_b(SeedState* st, cons
             const double ratio = rn / st->bnorm;
             if (ratio < 0x1p-20 || ratio > 0x1p20) f = -ilogb(ratio);
         }
-        st->rho = make_double2(ldexp(rho_new.x, 2 * f), ldexp(rho_new.y, 2 * f));
         st->rnorm = ldexp(rn, -st->sexp);
-        st->fexp = f;
-        st->sexp += f;
         s_rn = rn;
+        s_rho = rho_new;
         s_f = f;
         s_m = st->m;
     }
@@ -246,7 +248,9 @@ __global__ void __launch_bounds__(kScalarThreads) k_scalar_b(SeedState* st, cons
         const double rk = ldexp(s_rn / cabs(sh.zeta[k]), sh.zexp[k]);
         sh.iters[k] = s_m;
         sh.resid[k] = rk / st->bnorm;
-        sh.zexp[k] -= s_f;       // S_{m+1} = S_m 2^f
+        const double2 iz = cdiv(make_double2(1.0, 0.0), sh.zeta[k]);
+        sh.fz_coef[k] = make_double2(ldexp(iz.x, sh.zexp[k]), ldexp(iz.y, sh.zexp[k]));
+        sh.fz_iter[k] = s_m;
         if (rk <= thr) { sh.active[k] = 0; sh.conv[k] = 1; }
         else ++still;
     }
@@ -254,7 +258,24 @@ __global__ void __launch_bounds__(kScalarThreads) k_scalar_b(SeedState* st, cons
     block_sum<1>(cnt, sm);
     if (threadIdx.x == 0) {
         st->nactive = int(cnt[0]);
-        if (s_stop || cnt[0] == 0.0 || s_m >= st->maxit) st->done = 1;
+        if (s_stop || cnt[0] == 0.0 || s_m >= st->maxit) {
+            st->done = 1;
+            s_f = 0;                                   // nothing follows: keep r~ unscaled
+        }
+        const int f = s_f;
+        st->rho = make_double2(ldexp(s_rho.x, 2 * f), ldexp(s_rho.y, 2 * f));
+        st->fexp = f;
+        st->sexp += f;
+    }
+    __syncthreads();
+    if (s_f != 0) {
+        // S_{m+1} = S_m 2^f: exponents and residual factors of the shifts tested here
+        for (int k = threadIdx.x; k < ns; k += blockDim.x) {
+            if (sh.fz_iter[k] != s_m) continue;
+            sh.zexp[k] -= s_f;
+            const double2 c = sh.fz_coef[k];
+            sh.fz_coef[k] = make_double2(ldexp(c.x, -s_f), ldexp(c.y, -s_f));
+        }
     }
 }
 
@@ -295,11 +316,15 @@ __global__ void k_block_begin(SeedState* st, ShiftArrays sh, int ns) {
 // for i = 0 .. nblk[k]-1, P and x held in registers, r_i from the ring.
 // Optional row map: element e of the per-shift vectors is seed element
 // rows[e / rowlen] * rowlen + e % rowlen (only the rows the caller needs).
+// rrec (optional): for a shift that froze in this block, or for every shift with
+// pending iterations once the solve is done, its recursive residual at its last
+// tested iteration, fz_coef[k] * r~_{fz_iter[k]} (r~ from the ring).
 template <typename V, int BMAX>
 __global__ void __launch_bounds__(256) k_flush(const V* __restrict__ ring, int nslot, int64_t n_seed,
                                                V* __restrict__ P, V* __restrict__ X, int64_t n_out,
                                                const int32_t* __restrict__ rows, int64_t rowlen,
-                                               ShiftArrays sh, int ns, SeedState* __restrict__ st) {
+                                               ShiftArrays sh, int ns, SeedState* __restrict__ st,
+                                               V* __restrict__ rrec) {
     __shared__ int s_list[kMaxShifts];
     __shared__ int s_cnt;
     const int m0 = st->m0;
@@ -351,6 +376,12 @@ __global__ void __launch_bounds__(256) k_flush(const V* __restrict__ ring, int n
             }
             Pk[e] = pk;
             Xk[e] = xk;
+            if (rrec && (!sh.active[k] || st->done)) {
+                const int i = sh.fz_iter[k] - m0;                // 1 .. j
+                const V rf = ring[int64_t((slot0 + i) % nslot) * n_seed + src];
+                const double2 cf = sh.fz_coef[k];
+                rrec[int64_t(k) * n_out + e] = cscale(cf.x, cf.y, rf);
+            }
         }
     }
 }
@@ -423,6 +454,8 @@ __global__ void __launch_bounds__(kScalarThreads) k_init_state(SeedState* st, co
         sh.iters[k] = 0;
         sh.resid[k] = 0.0;
         sh.zexp[k] = 0;
+        sh.fz_coef[k] = make_double2(1.0, 0.0);
+        sh.fz_iter[k] = 0;
     }
 }
 
@@ -447,7 +480,8 @@ struct SolverImpl {
     DevBuf<SeedState> state;
     DevBuf<double2> zeta, zeta_prev, shift, coef64;
     DevBuf<C> coefv;
-    DevBuf<int> active, conv, broken, nblk, iters, zexp;
+    DevBuf<int> active, conv, broken, nblk, iters, zexp, fz_iter;
+    DevBuf<double2> fz_coef;
     DevBuf<double> resid;
     DevBuf<double2> shifts_dev;
     ShiftArrays sh{};
@@ -490,7 +524,8 @@ struct SolverImpl {
 #define MSB_FLUSH_CASE(BB)                                                                          \
     case BB:                                                                                        \
         k_flush<V, BB><<<grid_flush, 256, 0, st>>>(ring.p, nslot, pr.n, Pbuf.p, (V*)pr.x, pr.n_out, \
-                                                   pr.rows, pr.rowlen, sh, pr.ns, state.p);         \
+                                                   pr.rows, pr.rowlen, sh, pr.ns, state.p,          \
+                                                   (V*)pr.rrec);                                    \
         break;
             MSB_FLUSH_CASE(1) MSB_FLUSH_CASE(2) MSB_FLUSH_CASE(4) MSB_FLUSH_CASE(8) MSB_FLUSH_CASE(16)
 #undef MSB_FLUSH_CASE
@@ -526,11 +561,12 @@ struct SolverImpl {
         coef64.alloc(size_t(ns) * B * 2);
         coefv.alloc(size_t(ns) * B * 2);
         active.alloc(ns); conv.alloc(ns); broken.alloc(ns); nblk.alloc(ns); iters.alloc(ns); zexp.alloc(ns);
+        fz_iter.alloc(ns); fz_coef.alloc(ns);
         resid.alloc(ns);
         shifts_dev.alloc(ns);
         shifts_dev.upload(pr.shifts.data(), ns, st);
         sh = ShiftArrays{zeta.p, zeta_prev.p, shift.p, coef64.p, (void*)coefv.p,
-                         active.p, conv.p, broken.p, nblk.p, iters.p, resid.p, zexp.p};
+                         active.p, conv.p, broken.p, nblk.p, iters.p, resid.p, zexp.p, fz_coef.p, fz_iter.p};
 
         {
             ProfScope ps("seed_init", st, 3.0 * n * csz, 12.0 * n);

@@ -23,6 +23,8 @@ struct ShiftArrays {
     int* iters;           // iteration at freeze
     double* resid;        // ||r_m|| / (|zeta_m| ||b||) at freeze
     int* zexp;            // E_k = log2(g_k / S_m): exponent of the stored zeta pair
+    double2* fz_coef;     // r^k_m = fz_coef * (stored r~_m) for the shift's latest residual
+    int* fz_iter;         // the iteration m of that residual (Eq. 4 at freeze, or at the end)
 };
 
 struct SolveProblem {
@@ -33,6 +35,8 @@ struct SolveProblem {
     int64_t n_out = 0;        // per-shift vector length (n, or the projected length)
     const int32_t* rows = nullptr;   // optional row map for the projected output
     int64_t rowlen = 1;
+    void* rrec = nullptr;     // optional device output, ns x n_out: each shift's recursive
+                              // residual r_m / zeta_m^k (Eq. 4) at its freeze or at the end
     double2 c0{0, 0};
     std::vector<double2> shifts;
     double tol = 1e-10;

@@ -31,23 +31,34 @@ static void build_hubbard(msb_op* op, const msb_model& m, int intermediate) {
     op->sup.alloc(op->host_up.size()); op->sup.upload(op->host_up.data(), op->host_up.size());
     op->sdn.alloc(op->host_dn.size()); op->sdn.upload(op->host_dn.data(), op->host_dn.size());
     if (op->host_dn.size() < 32768) {
-        std::vector<uint16_t> t16(td.size());
-        // empty slots point at index Ddn, where the row-tiled FP32 apply keeps a zero
-        const uint16_t empty = uint16_t(op->host_dn.size() << 1);
-        for (size_t i = 0; i < td.size(); ++i) t16[i] = td[i] < 0 ? empty : uint16_t(td[i]);
+        // position-indexed copies for the continued fraction's row order
+        const int64_t D = int64_t(op->host_dn.size());
+        const std::vector<uint16_t>& ord = cached_row_order(m.L, op->sec_dn, m.periodic != 0);
+        MSB_REQUIRE(int64_t(ord.size()) == D, "row order size mismatch");
+        std::vector<int32_t> tpos;
+        std::vector<uint8_t> cpos;
+        table_in_row_order(td, cd, D, Wd, ord, tpos, cpos);
+        std::vector<uint32_t> spos(static_cast<size_t>(D));
+        for (int64_t p = 0; p < D; ++p) spos[p] = op->host_dn[ord[p]];
+        op->dpos.alloc(ord.size()); op->dpos.upload(ord.data(), ord.size());
+        op->ndnp.alloc(cpos.size()); op->ndnp.upload(cpos.data(), cpos.size());
+        op->sdnp.alloc(spos.size()); op->sdnp.upload(spos.data(), spos.size());
+        std::vector<uint16_t> t16(tpos.size());
+        // empty slots point at index Ddn, where the row-tiled apply keeps a zero
+        const uint16_t empty = uint16_t(D << 1);
+        for (size_t i = 0; i < tpos.size(); ++i) t16[i] = tpos[i] < 0 ? empty : uint16_t(tpos[i]);
         op->hdn16.alloc(t16.size());
         op->hdn16.upload(t16.data(), t16.size());
-        if (op->host_dn.size() % 2 == 0 && op->host_dn.size() >= 2) {
+        if (D % 2 == 0 && D >= 2) {
             // targets moved to their shared-memory slots for the FP32 row-tiled apply
-            const int64_t D = int64_t(op->host_dn.size());
             const RowLayout& lay = cached_row_layout(m.L, op->sec_dn, m.periodic != 0, kApplyThreads);
             MSB_REQUIRE(int64_t(lay.perm.size()) == D, "row layout size mismatch");
-            std::vector<uint16_t> tp(td.size());
-            for (size_t i = 0; i < td.size(); ++i) {
-                if (td[i] < 0) { tp[i] = empty; continue; }
-                const int32_t t = td[i] >> 1;
+            std::vector<uint16_t> tp(tpos.size());
+            for (size_t i = 0; i < tpos.size(); ++i) {
+                if (tpos[i] < 0) { tp[i] = empty; continue; }
+                const int32_t t = tpos[i] >> 1;
                 MSB_REQUIRE(t >= 0 && t < D, "hop target out of range");
-                tp[i] = uint16_t((int32_t(lay.perm[t]) << 1) | (td[i] & 1));
+                tp[i] = uint16_t((int32_t(lay.perm[t]) << 1) | (tpos[i] & 1));
             }
             for (uint16_t v : tp) MSB_REQUIRE((v >> 1) <= D, "permuted hop entry out of range");
             op->hdn16p.alloc(tp.size());
@@ -64,10 +75,20 @@ static void build_hubbard(msb_op* op, const msb_model& m, int intermediate) {
     h.Wdn = Wd;
     h.hup = op->hup.p; h.hdn = op->hdn.p;
     h.nup = op->nup.p; h.ndn = op->ndn.p;
+    h.dpos = op->dpos.p;
+    h.ndnp = op->ndnp.p;
+    h.sdnp = op->sdnp.p;
     h.hdn16 = op->hdn16.p;
     h.hdn16p = op->hdn16p.p;
     h.slot16 = op->slot16.p;
     h.sup = op->sup.p; h.sdn = op->sdn.p;
+    {
+        bool un = false, dn = false;
+        for (int32_t e : tu) un = un || (e >= 0 && (e & 1));
+        for (int32_t e : td) dn = dn || (e >= 0 && (e & 1));
+        h.usign = un ? 1 : 0;
+        h.dsign = dn ? 1 : 0;
+    }
     h.t = m.t; h.U = m.U; h.Uc = m.Uc;
     h.tf = float(m.t); h.Uf = float(m.U); h.Ucf = float(m.Uc);
     h.core = intermediate ? m.core_site : -1;

@@ -63,12 +63,19 @@ struct HubView {
     const int32_t* hdn;
     const uint8_t* nup;
     const uint8_t* ndn;
-    const uint16_t* hdn16;  // [slot][state] down-spin table with 16-bit entries (Ddn < 32768), else null;
+    // Continued-fraction row order (Ddn < 32768, else all null): the row-tiled
+    // apply kernels hold position p of a row as down state dpos[p] (states
+    // sorted by hop count) and use these position-indexed arrays.
+    const uint16_t* dpos;   // down state at position p
+    const uint8_t* ndnp;    // its hop count
+    const uint32_t* sdnp;   // its occupation string
+    const uint16_t* hdn16;  // [slot][position] down-spin table, entries (target position << 1) | neg;
                             // empty slots hold Ddn << 1 (index Ddn: a zero kept past the staged row)
     const uint16_t* hdn16p; // the same with targets moved to their shared-memory slots (FP32 apply), or null
-    const uint16_t* slot16; // shared-memory slot of each down-spin state (with hdn16p), or null
+    const uint16_t* slot16; // shared-memory slot of each position (with hdn16p), or null
     const uint32_t* sup;   // occupation strings, rank order
     const uint32_t* sdn;
+    int usign, dsign;      // 1 if some up / down hop carries a negative sign (ring bond, (-1)^(N-1) = -1)
     double t, U, Uc;
     int core;              // core-hole site, -1: none (plain H)
     int L;                 // sites
@@ -185,7 +192,9 @@ struct msb_op {
     int sec_up = 0, sec_dn = 0;  // electrons of this operator's sector
     msb::DevBuf<int32_t> hup, hdn;
     msb::DevBuf<uint8_t> nup, ndn;
-    msb::DevBuf<uint16_t> hdn16, hdn16p, slot16;
+    msb::DevBuf<uint16_t> hdn16, hdn16p, slot16, dpos;
+    msb::DevBuf<uint8_t> ndnp;
+    msb::DevBuf<uint32_t> sdnp;
     msb::DevBuf<uint32_t> sup, sdn;
     std::vector<uint32_t> host_up, host_dn;
     msb::HubView hub{};
@@ -224,6 +233,12 @@ struct RowLayout {
 RowLayout row_layout(const std::vector<int32_t>& table, const std::vector<uint8_t>& count, int64_t D, int W,
                      int threads);
 const RowLayout& cached_row_layout(int L, int n, bool periodic, int threads);
+// Continued-fraction row order (basis.cu): order[p] = down state at position p
+// of a row, sorted by hop count; the rank-space table rewritten to positions.
+std::vector<uint16_t> row_order(const std::vector<uint8_t>& count);
+const std::vector<uint16_t>& cached_row_order(int L, int n, bool periodic);
+void table_in_row_order(const std::vector<int32_t>& table, const std::vector<uint8_t>& count, int64_t D, int W,
+                        const std::vector<uint16_t>& ord, std::vector<int32_t>& tpos, std::vector<uint8_t>& cpos);
 // Host-side sector enumeration and hopping tables (basis.cu).
 std::vector<uint32_t> sector_states(int L, int n);
 // ELL hop table [W][D] with entries (target << 1) | neg, -1 empty; counts per state.

@@ -68,6 +68,7 @@ SIGNATURES = {
     "msb_basis_destroy": (None, [_P]),
     "msb_op_create_hubbard": (_I, [C.POINTER(msb_model), _I, C.POINTER(_P)]),
     "msb_basis_row_layout": (_I, [_P, _I, C.POINTER(C.c_uint16), _PD, _PD]),
+    "msb_basis_row_order": (_I, [_P, _I, C.POINTER(C.c_uint16)]),
     "msb_op_create_csr": (_I, [_I64, C.POINTER(C.c_int64), C.POINTER(C.c_int32), _PD, C.POINTER(_P)]),
     "msb_op_create_direct_sum": (_I, [C.POINTER(_P), _PD, _I, C.POINTER(_P)]),
     "msb_op_dim": (_I, [_P, C.POINTER(_I64)]),
@@ -79,6 +80,10 @@ SIGNATURES = {
     "msb_ground_state_noalloc": (_I, [_P, _D, _I, _P, _PD, _P, _PD, _P]),
     "msb_multishift_bicg_solve": (_I, [_P, msb_complex, _P, C.POINTER(msb_complex), _I, _D, _I, _I, _I, _P,
                                        _PI, _PD, _PI, C.POINTER(msb_solve_info), _P]),
+    "msb_bicgstab_solve": (_I, [_P, msb_complex, _P, C.POINTER(msb_complex), _I, _D, _I, _I, _P, _PI, _PD, _PI,
+                                C.POINTER(msb_solve_info), _P]),
+    "msb_multishift_bicg_reseeded": (_I, [_P, msb_complex, _P, C.POINTER(msb_complex), _I, _D, _I, _I, _I, _D, _I,
+                                          _I, _P, _PI, _PI, _PD, _PI, _PI, C.POINTER(msb_solve_info), _P]),
     "msb_continued_fraction": (_I, [_P, _P, _I, _D, _PD, _I, _D, _D, _I, _I, _I, _PD, _PI, _P]),
     "msb_rixs_map": (_I, [C.POINTER(msb_model), C.POINTER(msb_map_params), _P, _D, _PD, _I, _PD, _I, _PD,
                           C.POINTER(msb_solve_info), _P]),

@@ -1,27 +1,39 @@
-"""Host-side pieces of bench.py that need no GPU: which workloads the oracle's bounded
-CPU sample covers, and the JSON the reference arm prints where it does not."""
+"""Host-side pieces of bench.py that need no GPU: the oracle baseline on the host cores
+(the whole map of a small workload, rows over a process pool), which workloads it
+covers, and the JSON the reference arm prints where it does not."""
 import json
 import os
 import subprocess
 import sys
 
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 sys.path.insert(0, ROOT)
 
 
-def test_oracle_sample_bounds():
+def test_full_oracle_map_on_the_host_cores():
     import bench
-    assert bench.oracle_feasible("hubbard-L12-fp64")          # the default workload
-    assert bench.oracle_feasible("hubbard-L8-fp64")
-    assert not bench.oracle_feasible("hubbard-L14-mixed")     # D = 11.8 M
-    assert not bench.oracle_feasible("hubbard-L10-11-12-clusters-mixed")
-    r = bench.run_cpu_baseline("hubbard-L14-fp64")
+    import workloads
+    from oracle import rixs as orixs
+    wl = workloads.tiny(6, 3, 3)
+    r = bench.cpu_full_map(wl, return_map=True)
+    assert r["kind"] == "oracle" and r["cores"] >= 1 and r["value"] > 0
+    ref = orixs.rixs_map(6, 3, 3, 1.0, 8.0, 4.0, 0, wl.Gamma, wl.eta, wl.w_in, wl.w,
+                         gs_start=workloads.lanczos_start(400, wl.lanczos_seed))
+    assert orixs.relative_l2(r["map"], ref.I) <= 1e-10
+
+
+def test_baseline_coverage():
+    import bench
+    r = bench.run_cpu_baseline("hubbard-L10-11-12-clusters-mixed")
     assert r["value"] is None and r["kind"] == "oracle" and "not sampled" in r["sample"]
+    assert bench.DEFAULT == "hubbard-L14-mixed"
+    assert bench.host_cores() >= 1
 
 
 def test_reference_arm_unavailable_line():
     out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload",
-                          "hubbard-L14-mixed", "--steps", "1", "--warmup", "0"],
+                          "solve-sweep-L12", "--steps", "1", "--warmup", "0"],
                          capture_output=True, text=True, timeout=300, env=dict(os.environ, CUDA_VISIBLE_DEVICES=""))
     assert out.returncode == 0, out.stderr
     line = json.loads(out.stdout.strip().splitlines()[-1])

@@ -1,7 +1,9 @@
 """Bank-aware shared-memory placement of a down-spin row (host only, no device).
 
-The FP32 continued-fraction apply stages each row of V_k in shared memory and gathers the
-down-spin hop targets of 64 elements per warp (two per lane) one hop slot at a time.  The
+The continued-fraction apply holds each row in an order sorted by hop count (so that a
+warp's elements have equal trip counts); the FP32 kernel stages each row of V_k in shared
+memory and gathers the down-spin hop targets of 64 elements per warp (two per lane) one
+hop slot at a time.  The
 library chooses a slot per element so that the gathers of a half-warp hit fewer bank
 conflicts.  These tests recompute the access sets and their worst-bank counts in plain
 Python from the sector's hop structure, and check the library's numbers against them."""
@@ -28,6 +30,14 @@ def _down_hops(L, n, periodic=True):
     return hops
 
 
+def _in_row_order(hops):
+    """Hop lists by position: the states sorted by hop count (descending, stable),
+    targets renamed to their positions."""
+    order = sorted(range(len(hops)), key=lambda d: -len(hops[d]))
+    pos = {d: p for p, d in enumerate(order)}
+    return order, [[pos[t] for t in hops[d]] for d in order]
+
+
 def _mean_worst_bank(hops, slot):
     D = len(hops)
     half = D // 2
@@ -52,13 +62,23 @@ def _mean_worst_bank(hops, slot):
     return float(np.mean(costs))
 
 
+@pytest.mark.parametrize("L,n,periodic", [(8, 4, True), (12, 6, True), (10, 5, False), (7, 3, True)])
+def test_row_order_sorts_by_hop_count(L, n, periodic):
+    from paper_2506_09551_gb300 import api
+    order = api.row_order(L, n, periodic)
+    hops = _down_hops(L, n, periodic)
+    assert sorted(order.tolist()) == list(range(len(hops)))
+    ref, _ = _in_row_order(hops)
+    assert order.tolist() == ref
+
+
 @pytest.mark.parametrize("L,n", [(8, 4), (10, 5), (12, 6)])
 def test_layout_is_a_permutation_with_fewer_conflicts(L, n):
     from paper_2506_09551_gb300 import api
     slot, c_plain, c_layout = api.row_layout(L, n)
     D = len(slot)
     assert sorted(slot.tolist()) == list(range(D))
-    hops = _down_hops(L, n)
+    _, hops = _in_row_order(_down_hops(L, n))
     assert c_plain == pytest.approx(_mean_worst_bank(hops, range(D)), rel=1e-12)
     assert c_layout == pytest.approx(_mean_worst_bank(hops, slot), rel=1e-12)
     assert 1.0 <= c_layout < c_plain
@@ -69,7 +89,8 @@ def test_layout_is_a_permutation_with_fewer_conflicts(L, n):
 def test_open_chain_layout():
     from paper_2506_09551_gb300 import api
     slot, c_plain, c_layout = api.row_layout(10, 5, periodic=False)
-    assert c_layout == pytest.approx(_mean_worst_bank(_down_hops(10, 5, periodic=False), slot), rel=1e-12)
+    assert c_layout == pytest.approx(_mean_worst_bank(_in_row_order(_down_hops(10, 5, periodic=False))[1], slot),
+                                     rel=1e-12)
     assert c_layout <= c_plain
 
 

@@ -1,7 +1,7 @@
 """The allocation-free ground state, called through the C ABI.
 
 msb_ground_state_noalloc serves callers that cannot allocate device memory
-(inside a global-mode stream capture, or under another allocator's fixed
+(a process whose device memory belongs to another allocator under a fixed
 budget): it uses a fixed scratch array inside the library instead.  Checked
 here against the allocating msb_ground_state on two calls in a row, since the
 array keeps the previous call's contents.  This file is collected last so a
