@@ -143,6 +143,30 @@ def bonds(L: int, periodic: bool):
     return [(i, (i + 1) % L) for i in range(nb)]
 
 
+def cluster_bonds(L: int, periodic: bool = True, t: float = 1.0, lx: int = 0, tp: float = 0.0):
+    """Bonds (i, j, t_ij) of the lattice.  lx = 0: the 1D chain of `bonds` with hopping t.
+    lx > 0: the periodic lx x ly cluster (ly = L / lx, site x + lx y) with hopping t on
+    the nearest-neighbour bonds and t' = tp on the diagonal (next-nearest) bonds; both
+    sides must be at least 3 so that no bond is doubled by the wrap-around."""
+    if lx == 0:
+        return [(i, j, t) for (i, j) in bonds(L, periodic)]
+    if L % lx:
+        raise ValueError("L must be a multiple of lx")
+    ly = L // lx
+    if lx < 3 or ly < 3:
+        raise ValueError("a periodic 2D cluster needs both sides >= 3")
+    site = lambda x, y: (x % lx) + lx * (y % ly)  # noqa: E731
+    out = []
+    for y in range(ly):
+        for x in range(lx):
+            out.append((site(x, y), site(x + 1, y), t))
+            out.append((site(x, y), site(x, y + 1), t))
+            if tp != 0.0:
+                out.append((site(x, y), site(x + 1, y + 1), tp))
+                out.append((site(x, y), site(x - 1, y + 1), tp))
+    return out
+
+
 def hop_term(sec: Sector, i: int, j: int, spin: int):
     """COO triplets of c^dag_{j,s} c_{i,s} on `sec`: rows (new), cols (old), values."""
     oi = orbital(sec.L, i, spin, sec.order)
@@ -156,14 +180,15 @@ def hop_term(sec: Sector, i: int, j: int, spin: int):
 
 
 def hamiltonian(sec: Sector, t: float, U: float, Uc: float = 0.0, core_site: int | None = None,
-                periodic: bool = True) -> sp.csr_matrix:
-    """H of Eq. (9) on `sec`, plus -Uc (n_{j,up} + n_{j,dn}) of Eq. (10) when core_site is set."""
+                periodic: bool = True, bond_list=None) -> sp.csr_matrix:
+    """H of Eq. (9) on `sec`, plus -Uc (n_{j,up} + n_{j,dn}) of Eq. (10) when core_site is set.
+    bond_list: (i, j, t_ij) bonds (cluster_bonds); default the chain's bonds with hopping t."""
     R, C, V = [], [], []
-    for (i, j) in bonds(sec.L, periodic):
+    for (i, j, tij) in (bond_list if bond_list is not None else [(i, j, t) for (i, j) in bonds(sec.L, periodic)]):
         for s in (0, 1):
             for (a, b) in ((i, j), (j, i)):        # c^dag_b c_a and its h.c.
                 r, c, v = hop_term(sec, a, b, s)
-                R.append(r); C.append(c); V.append(-t * v)
+                R.append(r); C.append(c); V.append(-tij * v)
     diag = np.zeros(sec.dim)
     for i in range(sec.L):
         diag += U * (sec.occupation(i, 0) * sec.occupation(i, 1))
@@ -178,7 +203,7 @@ def hamiltonian(sec: Sector, t: float, U: float, Uc: float = 0.0, core_site: int
     return H
 
 
-def species_hops(L: int, n: int, t: float, periodic: bool = True) -> sp.csr_matrix:
+def species_hops(L: int, n: int, t: float, periodic: bool = True, bond_list=None) -> sp.csr_matrix:
     """Hopping matrix of one spin species alone: -t sum_<ij> (c^dag_j c_i + h.c.)
     on the L-bit strings with n set bits (rank order), with the textbook
     Jordan-Wigner sign computed by `annihilate` / `create` on those strings."""
@@ -186,12 +211,12 @@ def species_hops(L: int, n: int, t: float, periodic: bool = True) -> sp.csr_matr
     rank = np.full(1 << L, -1, dtype=np.int64)
     rank[states] = np.arange(len(states))
     R, C, V = [], [], []
-    for (i, j) in bonds(L, periodic):
+    for (i, j, tij) in (bond_list if bond_list is not None else [(i, j, t) for (i, j) in bonds(L, periodic)]):
         for (a, b) in ((i, j), (j, i)):
             a1, s1, mid = annihilate(states, a)
             a2, s2, new = create(mid, b)
             ok = a1 & a2
-            R.append(rank[new[ok]]); C.append(np.nonzero(ok)[0]); V.append(-t * (s1 * s2)[ok])
+            R.append(rank[new[ok]]); C.append(np.nonzero(ok)[0]); V.append(-tij * (s1 * s2)[ok])
     D = len(states)
     T = sp.coo_matrix((np.concatenate(V), (np.concatenate(R), np.concatenate(C))), shape=(D, D)).tocsr()
     T.sum_duplicates()
@@ -199,7 +224,7 @@ def species_hops(L: int, n: int, t: float, periodic: bool = True) -> sp.csr_matr
 
 
 def hamiltonian_kron(sec: Sector, t: float, U: float, Uc: float = 0.0, core_site: int | None = None,
-                     periodic: bool = True) -> sp.csr_matrix:
+                     periodic: bool = True, bond_list=None) -> sp.csr_matrix:
     """The same H (Eq. 9, plus the core-hole term of Eq. 10) assembled as
     T_up (x) I + I (x) T_dn + diag.  With the "up-first" orbital order every
     orbital strictly between two up orbitals is an up orbital (and likewise for
@@ -209,8 +234,8 @@ def hamiltonian_kron(sec: Sector, t: float, U: float, Uc: float = 0.0, core_site
     entry by entry (pinned in tests/test_oracle_model.py)."""
     if sec.order != "up-first":
         raise ValueError("the Kronecker form needs the up-first orbital order")
-    Tu = species_hops(sec.L, sec.n_up, t, periodic)
-    Td = species_hops(sec.L, sec.n_dn, t, periodic)
+    Tu = species_hops(sec.L, sec.n_up, t, periodic, bond_list)
+    Td = species_hops(sec.L, sec.n_dn, t, periodic, bond_list)
     diag = U * popcount(sec.u & sec.d).astype(np.float64)
     if core_site is not None:
         diag -= Uc * (sec.occupation(core_site, 0) + sec.occupation(core_site, 1))
@@ -241,7 +266,18 @@ def annihilation_operator(src: Sector, dst: Sector, site: int, spin: int) -> sp.
 
 @dataclass
 class RixsModel:
-    """H on the ground sector, H' on the intermediate sector, O2 and O1 (Eqs. 1, 2, 9, 10)."""
+    """H on the ground sector, H' on the intermediate sector, O2 and O1, and the
+    final-state H (Eqs. 1, 2, 9, 10).
+
+    O2 = c^dag_{j,spin} creates the excited electron with spin `spin`; O1 =
+    c_{j,spin_out} fills the core hole from the valence orbital with spin
+    `spin_out` (default: the same spin).  spin_out == spin is the spin-conserving
+    channel, whose final states lie in the ground sector; spin_out != spin is the
+    spin-flip channel, whose final states lie in the sector with one `spin_out`
+    electron fewer and one `spin` electron more (Sec. III's polarisation
+    channels, with the 2p orbitals reduced to one spin orbital).  lx > 0 makes
+    the lattice the periodic lx x (L / lx) cluster with diagonal hopping tp
+    (cluster_bonds)."""
     L: int
     n_up: int
     n_dn: int
@@ -252,13 +288,26 @@ class RixsModel:
     periodic: bool = True
     order: str = "up-first"
     spin: int = 0            # spin of the created electron: 0 = up (c^dag_{j,up})
+    spin_out: int | None = None
+    lx: int = 0
+    tp: float = 0.0
 
     def __post_init__(self):
+        if self.spin_out is None:
+            self.spin_out = self.spin
+        self.bonds = cluster_bonds(self.L, self.periodic, self.t, self.lx, self.tp)
         dn_shift = (1 if self.spin == 1 else 0)
         up_shift = (1 if self.spin == 0 else 0)
         self.gsec = Sector(self.L, self.n_up, self.n_dn, self.order)
         self.isec = Sector(self.L, self.n_up + up_shift, self.n_dn + dn_shift, self.order)
-        self.H = hamiltonian(self.gsec, self.t, self.U, periodic=self.periodic)
-        self.Hp = hamiltonian(self.isec, self.t, self.U, self.Uc, self.core_site, periodic=self.periodic)
+        fu = self.isec.n_up - (1 if self.spin_out == 0 else 0)
+        fd = self.isec.n_dn - (1 if self.spin_out == 1 else 0)
+        self.H = hamiltonian(self.gsec, self.t, self.U, bond_list=self.bonds)
+        self.Hp = hamiltonian(self.isec, self.t, self.U, self.Uc, self.core_site, bond_list=self.bonds)
+        if (fu, fd) == (self.n_up, self.n_dn):
+            self.fsec, self.Hf = self.gsec, self.H
+        else:
+            self.fsec = Sector(self.L, fu, fd, self.order)
+            self.Hf = hamiltonian(self.fsec, self.t, self.U, bond_list=self.bonds)
         self.O2 = creation_operator(self.gsec, self.isec, self.core_site, self.spin)
-        self.O1 = annihilation_operator(self.isec, self.gsec, self.core_site, self.spin)
+        self.O1 = annihilation_operator(self.isec, self.fsec, self.core_site, self.spin_out)

@@ -7,8 +7,9 @@ Pipeline (every step is the plain definition; nothing is fused or reordered):
   4. Psi_k = (H' - E_G - w_in_k - i Gamma)^{-1} E, each k solved on its own
      (Eq. 2 / Eq. A1; solvers.solve_shifted).
   5. phi_k = O1 Psi_k (Eq. 1).
-  6. I(w_in_k, w) = (1/pi) Im <phi_k|(H - E_G - w - i eta)^{-1}|phi_k> by the
-     continued fraction (spectrum.lanczos_cf), or by direct solves.
+  6. I(w_in_k, w) = (1/pi) Im <phi_k|(H_f - E_G - w - i eta)^{-1}|phi_k> by the
+     continued fraction (spectrum.lanczos_cf), or by direct solves; H_f is H on
+     the final sector (the ground sector in the spin-conserving channel).
 
 Parity: pinned by tests/test_oracle_spectrum.py against the Lehmann sum at
 L = 4 and 6, the atomic limit, the Kubo limit and the model's symmetries.
@@ -39,12 +40,12 @@ class MapResult:
 
 
 def rixs_map(L, n_up, n_dn, t, U, Uc, core_site, Gamma, eta, w_in, w, *, periodic=True,
-             order="up-first", spin=0, G=None, E_G=None, gs_tol=1e-12, gs_start=None,
-             solve_tol=1e-13, solve_method="auto", second_step="cf", cf_tol=1e-13,
+             order="up-first", spin=0, spin_out=None, lx=0, tp=0.0, G=None, E_G=None, gs_tol=1e-12,
+             gs_start=None, solve_tol=1e-13, solve_method="auto", second_step="cf", cf_tol=1e-13,
              model=None) -> MapResult:
     sec = {}
     t0 = time.perf_counter()
-    m = model or hubbard.RixsModel(L, n_up, n_dn, t, U, Uc, core_site, periodic, order, spin)
+    m = model or hubbard.RixsModel(L, n_up, n_dn, t, U, Uc, core_site, periodic, order, spin, spin_out, lx, tp)
     sec["build"] = time.perf_counter() - t0
     t0 = time.perf_counter()
     if G is None:
@@ -65,10 +66,10 @@ def rixs_map(L, n_up, n_dn, t, U, Uc, core_site, Gamma, eta, w_in, w, *, periodi
     depths = []
     for k in range(len(w_in)):
         if second_step == "cf":
-            I[k], d = spectrum.lanczos_cf(m.H, phi[k], E_G, np.asarray(w), eta, cf_tol=cf_tol)
+            I[k], d = spectrum.lanczos_cf(m.Hf, phi[k], E_G, np.asarray(w), eta, cf_tol=cf_tol)
             depths.append(d)
         else:
-            I[k] = spectrum.direct_second_step(m.H, phi[k], E_G, np.asarray(w), eta)
+            I[k] = spectrum.direct_second_step(m.Hf, phi[k], E_G, np.asarray(w), eta)
             depths.append(0)
     sec["second_step"] = time.perf_counter() - t0
     return MapResult(I, E_G, G, Psi, phi, nmv, depths, sec)
