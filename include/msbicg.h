@@ -185,7 +185,7 @@ msb_status msb_op_create_hubbard(const msb_model *model, int intermediate, msb_o
 msb_status msb_op_create_csr(int64_t n, const int64_t *rowptr, const int32_t *col,
                              const double *val, msb_op **out);
 
-/* Direct sum (block-diagonal operator) of n <= 4 Hubbard operators ops[i]
+/* Direct sum (block-diagonal operator) of n <= 16 Hubbard operators ops[i]
  * (from msb_op_create_hubbard), each with a real diagonal shift shifts[i]
  * (HOST array, NULL = all zero): A = (H_0 + s_0) (+) (H_1 + s_1) (+) ...
  * Vectors of A are the parts' vectors one after another (part 0 first).  One
@@ -195,7 +195,7 @@ msb_status msb_op_create_csr(int64_t n, const int64_t *rowptr, const int32_t *co
  * cluster's own E_G in every block and the shifts w_in - w_seed are common.
  * The parts are NOT owned: they must outlive the sum.  msb_ground_state and
  * msb_continued_fraction reject a direct sum (MSB_EINVAL).
- * Errors: MSB_EINVAL (n outside 1..4, a part that is not a Hubbard operator or
+ * Errors: MSB_EINVAL (n outside 1..16, a part that is not a Hubbard operator or
  * lives on another device, a non-finite shift). */
 msb_status msb_op_create_direct_sum(const msb_op *const *ops, const double *shifts, int n, msb_op **out);
 
@@ -348,6 +348,30 @@ msb_status msb_rixs_map(const msb_model *model, const msb_map_params *params,
                         void *stream);
 
 /* ------------------------------------------------------------------------ */
+/* Autotuner                                                                 */
+/* ------------------------------------------------------------------------ */
+
+/* Timed trials, on the operators of `model`, of the launch choices that leave
+ * the results unchanged up to the rounding order of a block reduction: the lag
+ * B in {1, 2, 4, 8, 16} of the fused per-shift update of a solve with n_in
+ * shifts (FP32 or FP64 per `prec`), and, for MSB_FP64, the threads per CTA
+ * (128 or 256) of the row-tiled continued-fraction apply.  Each candidate is
+ * timed with CUDA events as the difference of a 2K- and a K-iteration run (the
+ * allocations of a call cancel).  The fastest choices are cached for the whole
+ * process, keyed by the problem's shape (intermediate dimension, n_in and
+ * precision for B; row length, row count and precision for the threads), and
+ * used by every later call that leaves them automatic (params->block or the
+ * solver's `block` = 0).  HOST outputs (may be NULL): the choices, and the
+ * measured milliseconds per iteration for each B (5 values) and per level for
+ * each thread count (2 values, 0 for FP32).  Allocates and frees its own work
+ * vectors; synchronises `stream`.  The paper has no counterpart. */
+msb_status msb_autotune(const msb_model *model, msb_precision prec, int n_in, int *block, int *cf_threads,
+                        double *block_ms, double *cf_ms, void *stream);
+
+/* Forget every cached autotuned choice (later calls use the fixed defaults). */
+void msb_autotune_forget(void);
+
+/* ------------------------------------------------------------------------ */
 /* Kernel profiling                                                          */
 /* ------------------------------------------------------------------------ */
 
@@ -379,15 +403,17 @@ int msb_profile_read(msb_kernel_stat *out, int max);
 /* Maps for several right-hand sides of one model: O2 = c^dag_{j,up}, O1 =
  * c_{j,up} and the core hole on site j for every j in sites[n_sites] (Eqs. 1-2
  * per site; the batched workload of one cluster with one right-hand side per
- * core site).  One ground state; one multi-shift solve per site on that site's
- * H'; one continued fraction over all n_sites * n_in columns, which share H.
- * model->core_site is ignored.  I_out: HOST array n_sites x n_in x n_w (site
- * slowest).  Requires n_sites * n_in <= 65535.  Synchronises `stream`. */
+ * core site).  One ground state; ONE multi-shift solve on the direct sum of the
+ * sites' (H'_j - E_G) for the concatenated right-hand side (O2_j |G>)_j (every
+ * launch of the solve covers all sites); one continued fraction over all
+ * n_sites * n_in columns, which share H.  model->core_site is ignored.  I_out:
+ * HOST array n_sites x n_in x n_w (site slowest).  Requires n_sites <= 16 and
+ * n_sites * n_in <= 65535.  Synchronises `stream`. */
 msb_status msb_rixs_map_sites(const msb_model *model, const msb_map_params *params, const int *sites,
                               int n_sites, const double *w_in, int n_in, const double *w, int n_w,
                               double *I_out, msb_solve_info *info, void *stream);
 
-/* Maps of several independent clusters, models[n_clusters] (n_clusters <= 4;
+/* Maps of several independent clusters, models[n_clusters] (n_clusters <= 16;
  * any L, fillings, boundary and core site each), computed together: one FP64
  * ground state per cluster, then ONE multi-shift solve on the direct sum of
  * the clusters' (H'_c - E_G,c) for the concatenated right-hand side
@@ -404,14 +430,14 @@ msb_status msb_rixs_map_clusters(const msb_model *models, int n_clusters, const 
 
 /* Momentum-resolved maps (the coherent sum over core sites, Sec. III): for every
  * site j the map of msb_rixs_map_sites is formed up to phi_j = c_{j,up} Psi_j
- * (one ground state; one multi-shift solve per site on that site's H'), then
+ * (one ground state; one multi-shift solve over all sites' H'), then
  *   phi_q = sum_j exp(i q j) phi_j   and
  *   I_q(w_in, w) = (1/pi) Im <phi_q|(H - E_G - w - i eta)^{-1}|phi_q>
  * by one continued fraction over all n_q * n_in columns.  qs: HOST array of
  * n_q momenta (radians per site; over q = 2 pi k / L the maps sum to L times the
  * sum of the single-site maps).  model->core_site is ignored.  I_out: HOST array
  * n_q x n_in x n_w (q slowest).  Requires n_q * n_in <= 65535 and
- * L * n_in <= 65535.  Synchronises `stream`.  Errors as msb_rixs_map. */
+ * L * n_in <= 65535 (L <= 16).  Synchronises `stream`.  Errors as msb_rixs_map. */
 msb_status msb_rixs_map_q(const msb_model *model, const msb_map_params *params, const double *qs, int n_q,
                           const double *w_in, int n_in, const double *w, int n_w, double *I_out,
                           msb_solve_info *info, void *stream);

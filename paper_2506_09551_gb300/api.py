@@ -343,3 +343,21 @@ def rixs_map(m: N.msb_model, params: N.msb_map_params, w_in, w, G: torch.Tensor 
                                I.ctypes.data_as(C.POINTER(C.c_double)), C.byref(info), _stream())
     N.check(st, allow=allow_status)
     return I, info.as_dict(), st
+
+
+def autotune(m: N.msb_model, prec: int, n_in: int):
+    """Timed trials of the per-shift update lag and the FP64 continued-fraction CTA size
+    on this model; the choices are cached by the library for later calls.  Returns a dict."""
+    blk, thr = C.c_int(), C.c_int()
+    bms = np.zeros(5, dtype=np.float64)
+    cms = np.zeros(2, dtype=np.float64)
+    N.check(N.load().msb_autotune(C.byref(m), prec, n_in, C.byref(blk), C.byref(thr),
+                                  bms.ctypes.data_as(C.POINTER(C.c_double)), cms.ctypes.data_as(C.POINTER(C.c_double)),
+                                  _stream()))
+    return {"block": blk.value, "cf_threads": thr.value,
+            "ms_per_iteration": dict(zip((1, 2, 4, 8, 16), bms.tolist())),
+            "ms_per_level": dict(zip((128, 256), cms.tolist()))}
+
+
+def autotune_forget():
+    N.load().msb_autotune_forget()

@@ -1,0 +1,197 @@
+// Autotuner of the launch choices that leave the results unchanged (up to the
+// rounding of a block reduction): the lag B of the fused per-shift update of the
+// multi-shift solve (1, 2, 4, 8, 16 iterations per flush), and the threads per CTA
+// of the FP64 row-tiled continued-fraction apply (128 or 256).  Each candidate is
+// timed on the model's own operators with CUDA events, as the difference between
+// a run of 2K and a run of K iterations (or levels), so that the allocations of a
+// call cancel.  The fastest choice is cached per problem shape and used by every
+// call that leaves the choice on automatic (params->block == 0 for B; always for
+// the apply threads).
+#include <chrono>
+#include <cmath>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "kernels.cuh"
+#include "msbicg_impl.cuh"
+#include "profile.cuh"
+
+namespace msb {
+
+namespace {
+std::mutex g_tune_mu;
+std::map<std::tuple<int64_t, int, int>, int> g_tune_block;          // (n_seed, n_shifts, prec) -> B
+std::map<std::tuple<int64_t, int64_t, int>, int> g_tune_cf;         // (Ddn, Dup, prec) -> threads
+}  // namespace
+
+thread_local int g_cf_threads_force = 0;
+
+int tuned_block(int64_t n, int ns, msb_precision prec) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_block.find(std::make_tuple(n, ns, int(prec)));
+    return it == g_tune_block.end() ? 0 : it->second;
+}
+
+int tuned_cf_threads(int64_t Ddn, int64_t Dup, msb_precision prec) {
+    if (g_cf_threads_force) return g_cf_threads_force;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cf.find(std::make_tuple(Ddn, Dup, int(prec)));
+    return it == g_tune_cf.end() ? 0 : it->second;
+}
+
+void tune_forget() {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_block.clear();
+    g_tune_cf.clear();
+}
+
+// Seeded complex test vectors (splitmix64 of the index), values in (-1, 1).
+template <typename C>
+__global__ void k_tune_fill(C* v, int64_t n, uint64_t seed) {
+    using S = scalar_t<C>;
+    for (int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < n; s += int64_t(gridDim.x) * blockDim.x) {
+        uint64_t z = seed + 0x9E3779B97F4A7C15ull * uint64_t(s + 1);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        const double a = double(z >> 40) * (1.0 / 16777216.0) * 2.0 - 1.0;
+        const double b = double((z >> 16) & 0xFFFFFF) * (1.0 / 16777216.0) * 2.0 - 1.0;
+        v[s] = mk(S(a), S(b));
+    }
+}
+
+struct TuneOut {
+    int block = 0, cf_threads = 0;
+    double block_ms[5] = {0, 0, 0, 0, 0};
+    double cf_ms[2] = {0, 0};
+};
+
+template <typename C>
+static void autotune_impl(const msb_model& m, msb_precision prec, int n_in, TuneOut& out, cudaStream_t st) {
+    msb_op *a = nullptr, *b = nullptr;
+    msb_status s1 = msb_op_create_hubbard(&m, 0, &a);
+    if (s1 != MSB_OK) fail(s1, msb_last_error());
+    std::unique_ptr<msb_op> opH(a);
+    s1 = msb_op_create_hubbard(&m, 1, &b);
+    if (s1 != MSB_OK) fail(s1, msb_last_error());
+    std::unique_ptr<msb_op> opHp(b);
+    const int64_t Dp = opHp->dim, D = opH->dim, Ddn = opH->hub.Ddn;
+    // the rows the map carries per shift (core site up-occupied), as in the map's solve
+    const auto up_hi = sector_states(m.L, m.n_up + 1);
+    std::vector<int32_t> rows;
+    for (size_t r = 0; r < up_hi.size(); ++r)
+        if ((up_hi[r] >> m.core_site) & 1u) rows.push_back(int32_t(r));
+    DevBuf<int32_t> drows(rows.size());
+    drows.upload(rows.data(), rows.size(), st);
+    const int64_t n_out = int64_t(rows.size()) * Ddn;
+    DevBuf<C> rhs(Dp);
+    k_tune_fill<C><<<grid_for(Dp, 256, 4), 256, 0, st>>>(rhs.p, Dp, 0x7A11ull);
+    MSB_LAUNCH_CHECK();
+    cudaEvent_t e0, e1;
+    MSB_CUDA(cudaEventCreate(&e0));
+    MSB_CUDA(cudaEventCreate(&e1));
+    auto timed = [&](auto&& fn) {
+        MSB_CUDA(cudaEventRecord(e0, st));
+        fn();
+        MSB_CUDA(cudaEventRecord(e1, st));
+        MSB_CUDA(cudaEventSynchronize(e1));
+        float ms = 0;
+        MSB_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        return double(ms);
+    };
+    // 1. lag of the fused per-shift update
+    const int Bs[5] = {1, 2, 4, 8, 16};
+    const int K = 32;
+    {
+        DevBuf<C> X(size_t(n_in) * n_out);
+        double best = 1e300;
+        for (int i = 0; i < 5; ++i) {
+            auto run = [&](int maxit) {
+                SolveProblem pr;
+                pr.n = Dp;
+                pr.ns = n_in;
+                pr.b = rhs.p;
+                pr.x = X.p;
+                pr.n_out = n_out;
+                pr.rows = drows.p;
+                pr.rowlen = Ddn;
+                pr.c0 = make_double2(0.0, -0.3);
+                pr.tol = 0.0;
+                pr.maxit = maxit;
+                pr.block = Bs[i];
+                pr.prec = prec;
+                pr.shifts.resize(n_in);
+                for (int k = 0; k < n_in; ++k)
+                    pr.shifts[k] = make_double2(-4.0 + 16.0 * k / std::max(1, n_in - 1), 0.0);
+                SolveResult sr;
+                multishift_solve(opHp.get(), pr, sr, st);
+            };
+            run(K);                                    // warm-up
+            const double t1 = timed([&] { run(K); });
+            const double t2 = timed([&] { run(2 * K); });
+            out.block_ms[i] = std::max(t2 - t1, 0.0) / K;
+            if (out.block_ms[i] < best) { best = out.block_ms[i]; out.block = Bs[i]; }
+        }
+    }
+    // 2. threads per CTA of the FP64 row-tiled continued-fraction apply
+    if (prec == MSB_FP64) {
+        DevBuf<C> phi(size_t(n_in) * D);
+        k_tune_fill<C><<<grid_for(int64_t(n_in) * D, 256, 4), 256, 0, st>>>(phi.p, int64_t(n_in) * D, 0xCF11ull);
+        std::vector<double> w(8), I(size_t(n_in) * 8);
+        for (int i = 0; i < 8; ++i) w[i] = double(i);
+        const int Ts[2] = {128, 256};
+        double best = 1e300;
+        for (int i = 0; i < 2; ++i) {
+            g_cf_threads_force = Ts[i];
+            auto run = [&](int depth) {
+                CFResult cr;
+                continued_fraction(opH.get(), phi.p, n_in, 0.0, w.data(), 8, 0.1, 0.0, depth, depth, prec, I.data(),
+                                   cr, st, false);
+            };
+            try {
+                run(8);
+                const double t1 = timed([&] { run(16); });
+                const double t2 = timed([&] { run(32); });
+                out.cf_ms[i] = std::max(t2 - t1, 0.0) / 16;
+            } catch (...) {
+                g_cf_threads_force = 0;
+                throw;
+            }
+            g_cf_threads_force = 0;
+            if (out.cf_ms[i] < best) { best = out.cf_ms[i]; out.cf_threads = Ts[i]; }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_block[std::make_tuple(Dp, n_in, int(prec))] = out.block;
+    if (out.cf_threads) g_tune_cf[std::make_tuple(Ddn, opH->hub.Dup, int(prec))] = out.cf_threads;
+}
+
+}  // namespace msb
+
+extern "C" msb_status msb_autotune(const msb_model* model, msb_precision prec, int n_in, int* block,
+                                   int* cf_threads, double* block_ms, double* cf_ms, void* stream) {
+    return msb::guard("msb_autotune", [&] {
+        msb::require_device();
+        MSB_REQUIRE(model != nullptr, "model is NULL");
+        msb::validate_model(*model);
+        MSB_REQUIRE(model->n_up + 1 <= model->L, "the intermediate sector needs n_up + 1 <= L");
+        MSB_REQUIRE(prec == MSB_FP64 || prec == MSB_FP32_MIXED, "unknown precision");
+        MSB_REQUIRE(n_in >= 1 && n_in <= msb::kMaxShifts, "n_in must be in 1..4096");
+        msb::TuneOut out;
+        msb::StreamScope scope((cudaStream_t)stream);
+        if (prec == MSB_FP64) msb::autotune_impl<double2>(*model, prec, n_in, out, scope.s);
+        else msb::autotune_impl<float2>(*model, prec, n_in, out, scope.s);
+        scope.finish();
+        if (block) *block = out.block;
+        if (cf_threads) *cf_threads = out.cf_threads;
+        if (block_ms) for (int i = 0; i < 5; ++i) block_ms[i] = out.block_ms[i];
+        if (cf_ms) for (int i = 0; i < 2; ++i) cf_ms[i] = out.cf_ms[i];
+    });
+}
+
+extern "C" void msb_autotune_forget(void) { msb::tune_forget(); }

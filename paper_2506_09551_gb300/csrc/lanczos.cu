@@ -1191,6 +1191,10 @@ static void cf_impl(const CFColumns& P, const View& view, const double* w, int n
         // are paid over twice the work); longer rows keep 256 threads, where shared
         // memory, not registers, limits the CTAs per SM.
         fx_threads = maxDdn <= 1024 ? 128 : 256;
+        if (!multi && std::is_same<C, double2>::value) {
+            const int t = tuned_cf_threads(maxDdn, maxDup, MSB_FP64);
+            if (t == 128 || t == 256) fx_threads = t;
+        }
         fx = fx && rows;
         pair = pair && rows;
         if (rows) {

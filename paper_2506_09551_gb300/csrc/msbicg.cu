@@ -685,8 +685,11 @@ void multishift_solve(msb_op* op, const SolveProblem& pr, SolveResult& out, cuda
     }
 }
 
-int pick_block(int block, msb_precision prec) {
-    if (block == 0) return prec == MSB_FP64 ? 4 : 8;
+int pick_block(int block, msb_precision prec, int64_t n, int ns) {
+    if (block == 0) {
+        const int t = n > 0 ? tuned_block(n, ns, prec) : 0;
+        return t ? t : (prec == MSB_FP64 ? 4 : 8);
+    }
     MSB_REQUIRE(block == 1 || block == 2 || block == 4 || block == 8 || block == 16,
                 "block must be 0 (auto), 1, 2, 4, 8 or 16");
     return block;
@@ -720,7 +723,7 @@ extern "C" msb_status msb_multishift_bicg_solve(msb_op* A, msb_complex c0, const
         pr.c0 = make_double2(c0.re, c0.im);
         pr.tol = tol;
         pr.maxit = maxit;
-        pr.block = msb::pick_block(block, prec);
+        pr.block = msb::pick_block(block, prec, A->dim, n_shifts);
         pr.prec = prec;
         pr.shifts.resize(n_shifts);
         for (int k = 0; k < n_shifts; ++k) pr.shifts[k] = make_double2(shifts[k].re, shifts[k].im);

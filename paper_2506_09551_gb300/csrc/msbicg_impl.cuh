@@ -57,7 +57,12 @@ struct SolveResult {
 };
 
 void multishift_solve(msb_op* op, const SolveProblem& pr, SolveResult& out, cudaStream_t st);
-int pick_block(int block, msb_precision prec);
+// Lag B of the fused per-shift update: `block` if set, else the autotuned choice
+// for (n, ns, prec) if there is one (autotune.cu), else 4 (FP64) / 8 (FP32).
+int pick_block(int block, msb_precision prec, int64_t n = 0, int ns = 0);
+// Autotuned choices (0: none cached).
+int tuned_block(int64_t n, int ns, msb_precision prec);
+int tuned_cf_threads(int64_t Ddn, int64_t Dup, msb_precision prec);
 
 // Ground state by Lanczos (FP64, real vectors).
 struct GroundResult {

@@ -123,7 +123,7 @@ static void build_csr(msb_op* op, int64_t n, const int64_t* rowptr, const int32_
 }
 
 static void build_sum(msb_op* op, const msb_op* const* ops, const double* shifts, int n) {
-    MSB_REQUIRE(ops != nullptr && n >= 1 && n <= kMaxParts, "need 1..4 operators");
+    MSB_REQUIRE(ops != nullptr && n >= 1 && n <= kMaxParts, "need 1..16 operators");
     op->kind = 2;
     SumView& v = op->sum;
     v.np = n;

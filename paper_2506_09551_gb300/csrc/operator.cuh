@@ -125,7 +125,7 @@ struct HubView {
 // + shift[i] x[s].  One launch over the concatenated vector applies every part,
 // so one Krylov recurrence serves independent clusters of uneven size.
 // ----------------------------------------------------------------------------
-constexpr int kMaxParts = 4;
+constexpr int kMaxParts = 16;
 
 struct SumView {
     int np;
@@ -142,15 +142,20 @@ struct SumView {
 
     template <typename V>
     __device__ __forceinline__ V hx(int64_t s, const V* __restrict__ x, V xs) const {
-        // part index by comparison (no dynamic indexing of the parameter arrays)
-        if (np > 1 && s >= off[1]) {
-            if (np > 2 && s >= off[2]) {
-                if (np > 3 && s >= off[3]) return hx_part<3>(s, x, xs);
-                return hx_part<2>(s, x, xs);
-            }
-            return hx_part<1>(s, x, xs);
+        // part index by comparison with constant indices (no dynamic indexing of the
+        // parameter arrays), then a switch on it
+        int i = 0;
+#pragma unroll
+        for (int j = 1; j < kMaxParts; ++j)
+            if (j < np && s >= off[j]) i = j;
+        switch (i) {
+#define MSB_SUM_CASE(I) case I: return hx_part<I>(s, x, xs);
+            MSB_SUM_CASE(1) MSB_SUM_CASE(2) MSB_SUM_CASE(3) MSB_SUM_CASE(4) MSB_SUM_CASE(5) MSB_SUM_CASE(6)
+            MSB_SUM_CASE(7) MSB_SUM_CASE(8) MSB_SUM_CASE(9) MSB_SUM_CASE(10) MSB_SUM_CASE(11) MSB_SUM_CASE(12)
+            MSB_SUM_CASE(13) MSB_SUM_CASE(14) MSB_SUM_CASE(15)
+#undef MSB_SUM_CASE
+            default: return hx_part<0>(s, x, xs);
         }
-        return hx_part<0>(s, x, xs);
     }
 };
 

@@ -186,7 +186,7 @@ extern "C" msb_status msb_multishift_bicg_reseeded(msb_op* A, msb_complex c0, co
         for (int k = 0; k < n_shifts; ++k) s[k] = make_double2(shifts[k].re, shifts[k].im);
         msb::ReseedResult out;
         msb::StreamScope scope((cudaStream_t)stream);
-        const int B = msb::pick_block(block, prec);
+        const int B = msb::pick_block(block, prec, A->dim, n_shifts);
         if (prec == MSB_FP64)
             msb::reseeded_impl<double2>(A, make_double2(c0.re, c0.im), b, s, tol, maxit, B, prec, reseed_tol,
                                         seed_index, max_seeds, x, out, scope.s);

@@ -164,7 +164,7 @@ static msb_status solve_site(msb_op* opHp, const msb_op* opH, const msb_model& m
     pr.c0 = make_double2(-E_G - w_in[s0], -prm.Gamma);
     pr.tol = prm.solve_tol;
     pr.maxit = prm.maxit;
-    pr.block = pick_block(prm.block, prm.precision);
+    pr.block = pick_block(prm.block, prm.precision, pr.n, pr.ns);
     pr.prec = prm.precision;
     pr.shifts.resize(n_in);
     for (int k = 0; k < n_in; ++k) pr.shifts[k] = make_double2(w_in[k] - w_in[s0], 0.0);
@@ -330,6 +330,133 @@ __global__ void __launch_bounds__(256) k_qsum(const C* __restrict__ phi, int n_s
     }
 }
 
+// Steps 3-5 for several core sites j of one model in ONE multi-shift solve: the
+// block-diagonal operator A = (+)_j (H'_j - E_G) (one block per core site, each
+// with its own core hole) and the concatenated right-hand side (O2_j |G>)_j.  The
+// Krylov space of A keeps the blocks apart, so one recurrence (Alg. 1) solves
+// every site at every incident energy, and each launch of the solve covers all
+// sites.  Per-shift vectors carry only the rows each site's O1 reads.  The joint
+// residual bound tol * min_j ||b_j|| / ||b|| meets every site's own bound.
+// Phi: n_sites x n_in vectors of the ground sector (site slowest).
+static msb_status solve_sites_joint(const msb_op* opH, const msb_model& m, const msb_map_params& prm,
+                                    const int* sites, int n_sites, const double* G, double E_G, const double* w_in,
+                                    int n_in, char* Phi, msb_solve_info& info, cudaStream_t st, int64_t& launches) {
+    MSB_REQUIRE(n_sites >= 1 && n_sites <= kMaxParts, "need 1..16 core sites");
+    const int64_t D = opH->dim, Ddn = opH->hub.Ddn;
+    const size_t csz = prm.precision == MSB_FP64 ? sizeof(double2) : sizeof(float2);
+    std::vector<std::unique_ptr<msb_op>> opHp(n_sites);
+    for (int i = 0; i < n_sites; ++i) {
+        msb_model mj = m;
+        mj.core_site = sites[i];
+        msb_op* b = nullptr;
+        const msb_status s1 = msb_op_create_hubbard(&mj, 1, &b);
+        if (s1 != MSB_OK) fail(s1, msb_last_error());
+        opHp[i].reset(b);
+    }
+    const int64_t Dp = opHp[0]->dim;
+    const int64_t n = int64_t(n_sites) * Dp;
+    // right-hand side (O2_j |G>)_j; every block has norm ||c_{j,up}^dag G||
+    DevBuf<char> Ebuf(size_t(n) * csz);
+    std::vector<double> hg(D);
+    MSB_CUDA(cudaMemcpyAsync(hg.data(), G, D * sizeof(double), cudaMemcpyDeviceToHost, st));
+    MSB_CUDA(cudaStreamSynchronize(st));
+    double bmin = 0, b2 = 0;
+    // rows carried per shift: block i, intermediate up-rows with site j up-occupied
+    const auto up_hi = sector_states(m.L, m.n_up + 1);
+    const int64_t Dup_hi = int64_t(up_hi.size());
+    std::vector<int32_t> rows;
+    std::vector<std::vector<int32_t>> pos(n_sites, std::vector<int32_t>(up_hi.size(), -1));
+    for (int i = 0; i < n_sites; ++i) {
+        const int j = sites[i];
+        auto map = cdag_rowmap(m.L, m.n_up, j);
+        char* dst = Ebuf.p + size_t(i) * Dp * csz;
+        if (prm.precision == MSB_FP64)
+            launch_rowmap(G, (double2*)dst, map, Ddn, D, Dp, 1, st, launches);
+        else
+            launch_rowmap(G, (float2*)dst, map, Ddn, D, Dp, 1, st, launches);
+        double nb = 0;
+        for (size_t r = 0; r < map.size(); ++r) {
+            if (map[r] < 0) continue;
+            const double* gp = hg.data() + int64_t(map[r] >> 1) * Ddn;
+            for (int64_t d = 0; d < Ddn; ++d) nb += gp[d] * gp[d];
+        }
+        MSB_REQUIRE(nb > 0, "O2 annihilates the ground state (no intermediate state)");
+        bmin = i == 0 ? std::sqrt(nb) : std::min(bmin, std::sqrt(nb));
+        b2 += nb;
+        for (int64_t r = 0; r < Dup_hi; ++r)
+            if ((up_hi[r] >> j) & 1u) {
+                pos[i][r] = int32_t(rows.size());
+                rows.push_back(int32_t(int64_t(i) * Dup_hi + r));
+            }
+    }
+    DevBuf<int32_t> drows(rows.size());
+    drows.upload(rows.data(), rows.size(), st);
+    const int64_t n_out = int64_t(rows.size()) * Ddn;
+    std::vector<const msb_op*> parts(n_sites);
+    std::vector<double> shifts(n_sites, -E_G);
+    for (int i = 0; i < n_sites; ++i) parts[i] = opHp[i].get();
+    std::unique_ptr<msb_op> A;
+    {
+        msb_op* a = nullptr;
+        const msb_status s1 = msb_op_create_direct_sum(parts.data(), shifts.data(), n_sites, &a);
+        if (s1 != MSB_OK) fail(s1, msb_last_error());
+        A.reset(a);
+    }
+    int s0 = prm.seed_index;
+    if (s0 < 0) {
+        s0 = 0;
+        for (int k = 1; k < n_in; ++k) if (std::fabs(w_in[k]) < std::fabs(w_in[s0])) s0 = k;
+    }
+    MSB_REQUIRE(s0 < n_in, "seed_index out of range");
+    SolveProblem pr;
+    pr.n = n;
+    pr.ns = n_in;
+    pr.b = Ebuf.p;
+    pr.n_out = n_out;
+    pr.rows = drows.p;
+    pr.rowlen = Ddn;
+    pr.c0 = make_double2(-w_in[s0], -prm.Gamma);
+    pr.tol = prm.solve_tol * bmin / std::sqrt(b2);
+    pr.maxit = prm.maxit;
+    pr.block = pick_block(prm.block, prm.precision, pr.n, pr.ns);
+    pr.prec = prm.precision;
+    pr.shifts.resize(n_in);
+    for (int k = 0; k < n_in; ++k) pr.shifts[k] = make_double2(w_in[k] - w_in[s0], 0.0);
+    DevBuf<char> X(size_t(n_in) * n_out * csz);
+    pr.x = X.p;
+    SolveResult sr;
+    multishift_solve(A.get(), pr, sr, st);
+    MSB_CUDA(cudaStreamSynchronize(st));
+    launches += sr.launches;
+    info.iterations = std::max(info.iterations, sr.iterations);
+    info.n_converged += sr.n_converged;
+    info.flushes += sr.flushes;
+    info.seed_residual = std::max(info.seed_residual, sr.seed_residual);
+    for (double r : sr.resid) info.max_shift_residual = std::max(info.max_shift_residual, r);
+    info.matvecs += sr.iterations;
+    if (sr.status != MSB_OK && sr.status != MSB_EMAXITER) fail(sr.status, "multi-shift solve failed");
+    Ebuf.release();
+    // phi_{j,k} = O1_j Psi_{j,k} from the carried rows
+    const auto up_lo = sector_states(m.L, m.n_up);
+    auto rhi = rank_table(up_hi, m.L);
+    for (int i = 0; i < n_sites; ++i) {
+        const int j = sites[i];
+        std::vector<int32_t> omap(opH->hub.Dup, -1);
+        for (size_t r = 0; r < up_lo.size(); ++r) {
+            const uint32_t u = up_lo[r];
+            if ((u >> j) & 1u) continue;
+            const int32_t src = pos[i][rhi[u | (1u << j)]];
+            omap[r] = (src << 1) | jw_sign_below(u, j);
+        }
+        char* dst = Phi + size_t(i) * n_in * D * csz;
+        if (prm.precision == MSB_FP64)
+            launch_rowmap((const double2*)X.p, (double2*)dst, omap, Ddn, n_out, D, n_in, st, launches);
+        else
+            launch_rowmap((const float2*)X.p, (float2*)dst, omap, Ddn, n_out, D, n_in, st, launches);
+    }
+    return sr.status;
+}
+
 // Maps of several core sites (n_q = 0: one map per site), or their coherent sums
 // over the sites with momentum phases (n_q > 0: one map per q, Sec. III).
 static void rixs_map_sites_impl(const msb_model& m, const msb_map_params& prm, const int* sites, int n_sites,
@@ -367,18 +494,9 @@ static void rixs_map_sites_impl(const msb_model& m, const msb_map_params& prm, c
     t0 = std::chrono::steady_clock::now();
     const size_t csz = prm.precision == MSB_FP64 ? sizeof(double2) : sizeof(float2);
     DevBuf<char> Phi(size_t(n_sites) * n_in * D * csz);
-    bool maxit_hit = false;
-    for (int i = 0; i < n_sites; ++i) {
-        msb_model mj = m;
-        mj.core_site = sites[i];
-        msb_op* b = nullptr;
-        s1 = msb_op_create_hubbard(&mj, 1, &b);
-        if (s1 != MSB_OK) fail(s1, msb_last_error());
-        std::unique_ptr<msb_op> opHp(b);
-        const msb_status sst = solve_site(opHp.get(), opH.get(), mj, prm, g.p, gr.E, w_in, n_in,
-                                          Phi.p + size_t(i) * n_in * D * csz, info, st, launches);
-        maxit_hit |= sst == MSB_EMAXITER;
-    }
+    const msb_status sst = solve_sites_joint(opH.get(), m, prm, sites, n_sites, g.p, gr.E, w_in, n_in, Phi.p, info,
+                                             st, launches);
+    const bool maxit_hit = sst == MSB_EMAXITER;
     const void* cf_in = Phi.p;
     int n_cols = n_sites * n_in;
     DevBuf<char> Phiq;
@@ -435,7 +553,7 @@ static void rixs_map_sites_impl(const msb_model& m, const msb_map_params& prm, c
 static void rixs_map_clusters_impl(const msb_model* models, int nc, const msb_map_params& prm, const double* w_in,
                                    int n_in, const double* w, int n_w, double* I_out, double* E_out,
                                    msb_solve_info& info, cudaStream_t st) {
-    MSB_REQUIRE(models != nullptr && nc >= 1 && nc <= kMaxParts, "need 1..4 clusters");
+    MSB_REQUIRE(models != nullptr && nc >= 1 && nc <= kMaxParts, "need 1..16 clusters");
     MSB_REQUIRE(n_in >= 1 && n_in <= kMaxShifts && int64_t(nc) * n_in <= 65535,
                 "n_clusters * n_in must be at most 65535 (and n_in at most 4096)");
     MSB_REQUIRE(w_in && w && I_out && n_w >= 1, "NULL argument");
@@ -534,7 +652,7 @@ static void rixs_map_clusters_impl(const msb_model* models, int nc, const msb_ma
     pr.c0 = make_double2(-w_in[s0], -prm.Gamma);
     pr.tol = prm.solve_tol * bmin / std::sqrt(b2);
     pr.maxit = prm.maxit;
-    pr.block = pick_block(prm.block, prm.precision);
+    pr.block = pick_block(prm.block, prm.precision, pr.n, pr.ns);
     pr.prec = prm.precision;
     pr.shifts.resize(n_in);
     for (int k = 0; k < n_in; ++k) pr.shifts[k] = make_double2(w_in[k] - w_in[s0], 0.0);

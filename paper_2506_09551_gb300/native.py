@@ -82,6 +82,8 @@ SIGNATURES = {
                                        _PI, _PD, _PI, C.POINTER(msb_solve_info), _P]),
     "msb_bicgstab_solve": (_I, [_P, msb_complex, _P, C.POINTER(msb_complex), _I, _D, _I, _I, _P, _PI, _PD, _PI,
                                 C.POINTER(msb_solve_info), _P]),
+    "msb_autotune": (_I, [C.POINTER(msb_model), _I, _I, _PI, _PI, _PD, _PD, _P]),
+    "msb_autotune_forget": (None, []),
     "msb_multishift_bicg_reseeded": (_I, [_P, msb_complex, _P, C.POINTER(msb_complex), _I, _D, _I, _I, _I, _D, _I,
                                           _I, _P, _PI, _PI, _PD, _PI, _PI, C.POINTER(msb_solve_info), _P]),
     "msb_continued_fraction": (_I, [_P, _P, _I, _D, _PD, _I, _D, _D, _I, _I, _I, _PD, _PI, _P]),

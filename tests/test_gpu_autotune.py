@@ -1,0 +1,34 @@
+"""The autotuner: timed trials on the model's operators, cached choices used by later
+calls, and no effect on the results beyond rounding."""
+import numpy as np
+import pytest
+
+from oracle import rixs as orixs
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_autotune_choices_are_used_and_leave_the_map_unchanged(cuda, prec):
+    from paper_2506_09551_gb300 import api
+    wl = workloads.CHAIN8
+    m = api.model(wl.L, wl.n_up, wl.n_dn)
+    tol = dict(solve_tol=1e-10, cf_tol=1e-9) if prec == 0 else dict(solve_tol=1e-8, cf_tol=1e-5)
+    api.autotune_forget()
+    I_fixed, info_f, _ = api.rixs_map(m, api.map_params(precision=prec, block=4 if prec == 0 else 8, **tol),
+                                      wl.w_in, wl.w)
+    t = api.autotune(m, prec, wl.n_in)
+    assert t["block"] in (1, 2, 4, 8, 16)
+    assert all(v > 0 for v in t["ms_per_iteration"].values())
+    if prec == 0:
+        assert t["cf_threads"] in (128, 256) and all(v > 0 for v in t["ms_per_level"].values())
+    else:
+        assert t["cf_threads"] == 0
+    I_tuned, info_t, _ = api.rixs_map(m, api.map_params(precision=prec, block=0, **tol), wl.w_in, wl.w)
+    I_expl, _, _ = api.rixs_map(m, api.map_params(precision=prec, block=t["block"], **tol), wl.w_in, wl.w)
+    # the lag of the per-shift update is bitwise neutral; the CTA size only reorders a block sum
+    assert np.array_equal(I_tuned, I_expl) or orixs.relative_l2(I_tuned, I_expl) <= 1e-13
+    assert orixs.relative_l2(I_tuned, I_fixed) <= (1e-11 if prec == 0 else 1e-6)
+    assert info_t["flushes"] != info_f["flushes"] or t["block"] == (4 if prec == 0 else 8)
+    api.autotune_forget()
