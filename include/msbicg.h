@@ -58,18 +58,29 @@ typedef enum {
 
 typedef struct { double re, im; } msb_complex;
 
-/* Hubbard chain and RIXS transition (Eqs. 9-10; Sec. III).
- * H' = H - Uc (n_{j,up} + n_{j,dn}) on the (n_up + 1, n_dn) sector: the core
- * hole sits on the site j = core_site where O2 = c^dag_{j,up} acted, and the
- * edge energy E_edge is absorbed into w_in. */
+/* Hubbard cluster and RIXS transition (Eqs. 9-10; Sec. III).
+ * H' = H - Uc (n_{j,up} + n_{j,dn}) on the sector with the O2 electron added:
+ * the core hole sits on the site j = core_site where O2 = c^dag_{j,o2_spin}
+ * acted, and the edge energy E_edge is absorbed into w_in.  O1 = c_{j,o1_spin}
+ * fills the core hole; o1_spin == o2_spin is the spin-conserving channel (final
+ * states in the ground sector), o1_spin != o2_spin the spin-flip channel (final
+ * states with one o1_spin electron fewer and one o2_spin electron more).  A
+ * zero-initialised tail (o2_spin = o1_spin = lx = 0, tp = 0) is the up-spin
+ * channel on a chain. */
 typedef struct {
     int L;            /* sites, 3 <= L <= 16 for a ring, 2 <= L <= 16 open       */
     int n_up, n_dn;   /* electrons of the ground-state sector                    */
-    int periodic;     /* 1: ring (bond L-1 -- 0 carries sign (-1)^(N_s - 1)); 0: open */
+    int periodic;     /* chain: 1 ring, 0 open (ignored for a 2D cluster)        */
     double t;         /* nearest-neighbour hopping (Eq. 9)                       */
     double U;         /* on-site repulsion (Eq. 9)                               */
     double Uc;        /* core-hole potential (Eq. 10)                            */
-    int core_site;    /* j of O2 = c^dag_{j,up}, O1 = c_{j,up}                  */
+    int core_site;    /* j of O2 = c^dag_{j,o2_spin}, O1 = c_{j,o1_spin}          */
+    int o2_spin;      /* 0 = up, 1 = down                                        */
+    int o1_spin;      /* 0 = up, 1 = down                                        */
+    int lx;           /* 0: chain of L sites; > 0: periodic lx x (L / lx) cluster,
+                         site x + lx y, lx >= 3 and L / lx >= 3                  */
+    double tp;        /* diagonal (next-nearest-neighbour) hopping t' of a 2D
+                         cluster; bonds (x,y)-(x+1,y+1) and (x,y)-(x-1,y+1)      */
 } msb_model;
 
 /* Parameters of the whole map (Eqs. 1-2). */
@@ -173,11 +184,15 @@ msb_status msb_basis_row_layout(const msb_basis *b, int periodic, uint16_t *slot
 /* Operators A = H, H' (matrix-free) or a user CSR matrix                    */
 /* ------------------------------------------------------------------------ */
 
-/* Matrix-free Hubbard operator.  intermediate = 0: H of Eq. (9) on the
- * (n_up, n_dn) sector; intermediate = 1: H' of Eq. (10) on (n_up + 1, n_dn).
- * The hopping tables are built on the host and copied to the current device.
- * Errors: MSB_EINVAL (model out of range), MSB_ECUDA, MSB_ENOMEM. */
-msb_status msb_op_create_hubbard(const msb_model *model, int intermediate, msb_op **out);
+/* Matrix-free Hubbard operator (Eq. 9 on the model's chain or 2D cluster).
+ * sector = 0: H on the ground sector (n_up, n_dn); 1: H' of Eq. (10) on the
+ * intermediate sector, the ground sector plus the O2 electron (o2_spin), with
+ * the core hole on core_site; 2: H on the final sector, the intermediate
+ * sector minus the O1 electron (o1_spin) -- the ground sector again unless the
+ * channel flips the spin.  The hopping tables are built on the host and copied
+ * to the current device.
+ * Errors: MSB_EINVAL (model or sector out of range), MSB_ECUDA, MSB_ENOMEM. */
+msb_status msb_op_create_hubbard(const msb_model *model, int sector, msb_op **out);
 
 /* General real symmetric sparse matrix in CSR form (HOST arrays: rowptr[n+1],
  * col[nnz], val[nnz]); copied to the device.  Symmetry is assumed, not checked;

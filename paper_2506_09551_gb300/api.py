@@ -33,8 +33,12 @@ def cdtype(prec: int) -> torch.dtype:
     return torch.complex128 if prec == FP64 else torch.complex64
 
 
-def model(L, n_up, n_dn, t=1.0, U=8.0, Uc=4.0, core_site=0, periodic=True) -> N.msb_model:
-    return N.msb_model(L, n_up, n_dn, 1 if periodic else 0, t, U, Uc, core_site)
+def model(L, n_up, n_dn, t=1.0, U=8.0, Uc=4.0, core_site=0, periodic=True, o2_spin=0, o1_spin=None, lx=0,
+          tp=0.0) -> N.msb_model:
+    """A Hubbard chain (lx = 0) or periodic lx x (L / lx) cluster with diagonal hopping tp, and
+    the RIXS channel O2 = c^dag_{j,o2_spin}, O1 = c_{j,o1_spin} (o1_spin defaults to o2_spin)."""
+    o1 = o2_spin if o1_spin is None else o1_spin
+    return N.msb_model(L, n_up, n_dn, 1 if periodic else 0, t, U, Uc, core_site, o2_spin, o1, lx, tp)
 
 
 def map_params(**kw) -> N.msb_map_params:
@@ -107,9 +111,11 @@ class Operator:
         self.dim = d.value
 
     @classmethod
-    def hubbard(cls, m: N.msb_model, intermediate: bool = False) -> "Operator":
+    def hubbard(cls, m: N.msb_model, sector=False) -> "Operator":
+        """H on the model's ground sector (sector 0 / False), H' on the intermediate sector
+        (1 / True) or H on the final sector of a spin-flip channel (2)."""
         h = C.c_void_p()
-        N.check(N.load().msb_op_create_hubbard(C.byref(m), 1 if intermediate else 0, C.byref(h)))
+        N.check(N.load().msb_op_create_hubbard(C.byref(m), int(sector), C.byref(h)))
         return cls(h)
 
     @classmethod

@@ -8,6 +8,7 @@
 // carries (-1)^(N_s - 1).  The down species never picks up a sign from the up
 // orbitals because they are passed twice (once by c, once by c^dag).
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <tuple>
 #include <mutex>
@@ -29,30 +30,65 @@ std::vector<uint32_t> sector_states(int L, int n) {
     return s;  // ascending = rank order
 }
 
-void hop_table(int L, int n, bool periodic, const std::vector<uint32_t>& states,
-               std::vector<int32_t>& table, std::vector<uint8_t>& count, int& W) {
+std::vector<Bond> lattice_bonds(int L, bool periodic, int lx, bool diag) {
+    std::vector<Bond> out;
+    if (lx == 0) {
+        const int nb = periodic ? L : L - 1;
+        for (int i = 0; i < nb; ++i) out.push_back({i, (i + 1) % L, 0});
+        return out;
+    }
+    const int ly = L / lx;
+    auto site = [&](int x, int y) { return ((x % lx + lx) % lx) + lx * ((y % ly + ly) % ly); };
+    for (int y = 0; y < ly; ++y)
+        for (int x = 0; x < lx; ++x) {
+            out.push_back({site(x, y), site(x + 1, y), 0});
+            out.push_back({site(x, y), site(x, y + 1), 0});
+            if (diag) {
+                out.push_back({site(x, y), site(x + 1, y + 1), 1});
+                out.push_back({site(x, y), site(x - 1, y + 1), 1});
+            }
+        }
+    return out;
+}
+
+// ELL hop table of the bonds of class `cls` for one species with n electrons.
+// Sign: with all orbitals of one species consecutive in the Jordan-Wigner order,
+// a hop between sites a < b passes the occupied orbitals of that species strictly
+// between a and b, (-1)^(their number).  (On the ring this is -1 only for the bond
+// L-1 -- 0 with an even electron count: (-1)^(N - 1).)
+void hop_table_bonds(const std::vector<Bond>& bonds, int cls, int L, int n, const std::vector<uint32_t>& states,
+                     std::vector<int32_t>& table, std::vector<uint8_t>& count, int& W) {
+    (void)n;
     const int64_t D = int64_t(states.size());
     std::vector<int32_t> rank(size_t(1) << L, -1);
     for (int64_t i = 0; i < D; ++i) rank[states[i]] = int32_t(i);
-    const int nb = periodic ? L : L - 1;
+    std::vector<Bond> bs;
+    for (const Bond& b : bonds) if (b.cls == cls) bs.push_back(b);
+    const int nb = int(bs.size());
     W = std::max(nb, 1);
+    MSB_REQUIRE(W <= 255, "too many bonds for the hop table");
     table.assign(size_t(W) * D, -1);
     count.assign(size_t(D), 0);
-    const bool ring_neg = periodic && ((n - 1) & 1);
     for (int64_t k = 0; k < D; ++k) {
         const uint32_t s = states[k];
         int c = 0;
-        for (int i = 0; i < nb; ++i) {
-            const int j = (i + 1) % L;
-            const uint32_t bi = (s >> i) & 1u, bj = (s >> j) & 1u;
+        for (const Bond& b : bs) {
+            const uint32_t bi = (s >> b.i) & 1u, bj = (s >> b.j) & 1u;
             if (bi == bj) continue;
-            const uint32_t tgt = s ^ (1u << i) ^ (1u << j);
-            const bool neg = (j == 0) && ring_neg;
+            const int lo = std::min(b.i, b.j), hi = std::max(b.i, b.j);
+            const uint32_t between = ((1u << hi) - 1u) & ~((1u << (lo + 1)) - 1u);
+            const bool neg = __builtin_popcount(s & between) & 1;
+            const uint32_t tgt = s ^ (1u << b.i) ^ (1u << b.j);
             table[size_t(c) * D + k] = (rank[tgt] << 1) | (neg ? 1 : 0);
             ++c;
         }
         count[k] = uint8_t(c);
     }
+}
+
+void hop_table(int L, int n, bool periodic, const std::vector<uint32_t>& states,
+               std::vector<int32_t>& table, std::vector<uint8_t>& count, int& W, int lx) {
+    hop_table_bonds(lattice_bonds(L, periodic, lx, false), 0, L, n, states, table, count, W);
 }
 
 // ---------------------------------------------------------------------------
@@ -223,36 +259,36 @@ void table_in_row_order(const std::vector<int32_t>& table, const std::vector<uin
     }
 }
 
-const std::vector<uint16_t>& cached_row_order(int L, int n, bool periodic) {
+const std::vector<uint16_t>& cached_row_order(int L, int n, bool periodic, int lx) {
     static std::mutex mu;
-    static std::map<std::tuple<int, int, bool>, std::vector<uint16_t>> cache;
+    static std::map<std::tuple<int, int, bool, int>, std::vector<uint16_t>> cache;
     std::lock_guard<std::mutex> lock(mu);
-    const auto key = std::make_tuple(L, n, periodic);
+    const auto key = std::make_tuple(L, n, periodic, lx);
     auto it = cache.find(key);
     if (it != cache.end()) return it->second;
     const auto states = sector_states(L, n);
     std::vector<int32_t> table;
     std::vector<uint8_t> count;
     int W = 0;
-    hop_table(L, n, periodic, states, table, count, W);
+    hop_table(L, n, periodic, states, table, count, W, lx);
     return cache.emplace(key, row_order(count)).first->second;
 }
 
 // Bank-aware placement of the row in its continued-fraction order (the kernel
 // gathers by position).
-const RowLayout& cached_row_layout(int L, int n, bool periodic, int threads) {
+const RowLayout& cached_row_layout(int L, int n, bool periodic, int threads, int lx) {
     static std::mutex mu;
-    static std::map<std::tuple<int, int, bool, int>, RowLayout> cache;
-    const auto& ord = cached_row_order(L, n, periodic);
+    static std::map<std::tuple<int, int, bool, int, int>, RowLayout> cache;
+    const auto& ord = cached_row_order(L, n, periodic, lx);
     std::lock_guard<std::mutex> lock(mu);
-    const auto key = std::make_tuple(L, n, periodic, threads);
+    const auto key = std::make_tuple(L, n, periodic, threads, lx);
     auto it = cache.find(key);
     if (it != cache.end()) return it->second;
     const auto states = sector_states(L, n);
     std::vector<int32_t> table, tpos;
     std::vector<uint8_t> count, cpos;
     int W = 0;
-    hop_table(L, n, periodic, states, table, count, W);
+    hop_table(L, n, periodic, states, table, count, W, lx);
     table_in_row_order(table, count, int64_t(states.size()), W, ord, tpos, cpos);
     return cache.emplace(key, row_layout(tpos, cpos, int64_t(states.size()), W, threads)).first->second;
 }
@@ -263,6 +299,11 @@ void validate_model(const msb_model& m) {
     MSB_REQUIRE(m.n_up >= 0 && m.n_up <= m.L && m.n_dn >= 0 && m.n_dn <= m.L,
                 "electron counts must be in 0..L");
     MSB_REQUIRE(m.core_site >= 0 && m.core_site < m.L, "core_site must be in 0..L-1");
+    MSB_REQUIRE((m.o2_spin == 0 || m.o2_spin == 1) && (m.o1_spin == 0 || m.o1_spin == 1),
+                "o2_spin and o1_spin must be 0 (up) or 1 (down)");
+    MSB_REQUIRE(m.lx == 0 || (m.lx >= 3 && m.L % m.lx == 0 && m.L / m.lx >= 3),
+                "a 2D cluster needs lx >= 3 dividing L with L / lx >= 3");
+    MSB_REQUIRE(std::isfinite(m.tp) && (m.tp == 0.0 || m.lx > 0), "tp needs a 2D cluster (lx > 0)");
 }
 
 }  // namespace msb

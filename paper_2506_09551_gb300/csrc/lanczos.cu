@@ -495,7 +495,7 @@ struct CFCoef {
     float* cCf;
 };
 
-constexpr int kMaxHops = 16;
+constexpr int kMaxHops = 32;     // up-spin hops per row (a 2D 3 x 4 cluster has 24 bonds)
 
 // Pass A for the Hubbard operator, one CTA per (row u, active column): row u
 // of V_k is staged in shared memory (own values and the down-spin gathers);
@@ -1180,7 +1180,8 @@ static void cf_impl(const CFColumns& P, const View& view, const double* w, int n
             maxDdn = std::max(maxDdn, h.Ddn);
             maxDup = std::max(maxDup, h.Dup);
             maxL = std::max(maxL, h.L);
-            rows = rows && h.Wup <= kMaxHops && h.Dup * h.Ddn < (int64_t(1) << 31) && h.hdn16 != nullptr;
+            rows = rows && h.Wup <= kMaxHops && h.Dup * h.Ddn < (int64_t(1) << 31) && h.hdn16 != nullptr &&
+                   h.hup2 == nullptr;      // the row-tiled kernels apply one hopping amplitude
             pair = pair && h.Ddn % 2 == 0;
             sgn = sgn || h.usign || h.dsign;
         }
@@ -1211,7 +1212,7 @@ static void cf_impl(const CFColumns& P, const View& view, const double* w, int n
             MSB_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(hub_smem)));
         }
     }
-    MSB_REQUIRE(!multi || rows, "a batch of clusters needs the row-tiled Hubbard apply (L <= 16, <= 16 hops)");
+    MSB_REQUIRE(!multi || rows, "a batch of clusters needs the row-tiled Hubbard apply (one hopping amplitude)");
     DevBuf<C> Q(3 * size_t(nv) * ld);
     DevBuf<double> part(size_t(std::max(grid, nblkA)) * nv), a(size_t(maxdepth) * nv), b(size_t(maxdepth) * nv),
         n0(nv), sig(nv), cB(nv), cC(nv), I(size_t(nv) * n_w), diff(2 * size_t(nv)), wdev(n_w), E0d(nv);

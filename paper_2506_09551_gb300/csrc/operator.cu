@@ -8,21 +8,51 @@
 
 namespace msb {
 
+// Electron counts of the model's sectors: 0 ground, 1 intermediate (after O2 =
+// c^dag_{j,o2_spin}), 2 final (after O1 = c_{j,o1_spin}).
+void model_sector(const msb_model& m, int which, int& n_up, int& n_dn) {
+    n_up = m.n_up;
+    n_dn = m.n_dn;
+    if (which >= 1) (m.o2_spin == 0 ? n_up : n_dn) += 1;
+    if (which == 2) (m.o1_spin == 0 ? n_up : n_dn) -= 1;
+}
+
 static void build_hubbard(msb_op* op, const msb_model& m, int intermediate) {
     validate_model(m);
-    MSB_REQUIRE(!intermediate || m.n_up + 1 <= m.L, "intermediate sector needs n_up + 1 <= L");
+    MSB_REQUIRE(intermediate >= 0 && intermediate <= 2, "sector must be 0 (ground), 1 (intermediate) or 2 (final)");
+    int nu = 0, nd = 0;
+    model_sector(m, intermediate, nu, nd);
+    MSB_REQUIRE(nu >= 0 && nu <= m.L && nd >= 0 && nd <= m.L, "the sector's electron counts must be in 0..L");
     op->kind = 0;
     op->model = m;
     op->intermediate = intermediate;
-    op->sec_up = m.n_up + (intermediate ? 1 : 0);
-    op->sec_dn = m.n_dn;
+    op->sec_up = nu;
+    op->sec_dn = nd;
     op->host_up = sector_states(m.L, op->sec_up);
     op->host_dn = sector_states(m.L, op->sec_dn);
     std::vector<int32_t> tu, td;
     std::vector<uint8_t> cu, cd;
     int Wu = 0, Wd = 0;
-    hop_table(m.L, op->sec_up, m.periodic != 0, op->host_up, tu, cu, Wu);
-    hop_table(m.L, op->sec_dn, m.periodic != 0, op->host_dn, td, cd, Wd);
+    hop_table(m.L, op->sec_up, m.periodic != 0, op->host_up, tu, cu, Wu, m.lx);
+    hop_table(m.L, op->sec_dn, m.periodic != 0, op->host_dn, td, cd, Wd, m.lx);
+    if (m.lx > 0 && m.tp != 0.0) {
+        const auto bonds = lattice_bonds(m.L, true, m.lx, true);
+        std::vector<int32_t> tu2, td2;
+        std::vector<uint8_t> cu2, cd2;
+        int Wu2 = 0, Wd2 = 0;
+        hop_table_bonds(bonds, 1, m.L, op->sec_up, op->host_up, tu2, cu2, Wu2);
+        hop_table_bonds(bonds, 1, m.L, op->sec_dn, op->host_dn, td2, cd2, Wd2);
+        op->hup2.alloc(tu2.size()); op->hup2.upload(tu2.data(), tu2.size());
+        op->hdn2.alloc(td2.size()); op->hdn2.upload(td2.data(), td2.size());
+        op->nup2.alloc(cu2.size()); op->nup2.upload(cu2.data(), cu2.size());
+        op->ndn2.alloc(cd2.size()); op->ndn2.upload(cd2.data(), cd2.size());
+        op->hub.Wup2 = Wu2;
+        op->hub.Wdn2 = Wd2;
+        double nh2 = 0;
+        for (uint8_t c : cu2) nh2 += double(c) * double(cd.size());
+        for (uint8_t c : cd2) nh2 += double(c) * double(cu.size());
+        op->offdiag2 = nh2;
+    }
     MSB_CUDA(cudaGetDevice(&op->device));
     op->hup.alloc(tu.size()); op->hup.upload(tu.data(), tu.size());
     op->hdn.alloc(td.size()); op->hdn.upload(td.data(), td.size());
@@ -33,7 +63,7 @@ static void build_hubbard(msb_op* op, const msb_model& m, int intermediate) {
     if (op->host_dn.size() < 32768) {
         // position-indexed copies for the continued fraction's row order
         const int64_t D = int64_t(op->host_dn.size());
-        const std::vector<uint16_t>& ord = cached_row_order(m.L, op->sec_dn, m.periodic != 0);
+        const std::vector<uint16_t>& ord = cached_row_order(m.L, op->sec_dn, m.periodic != 0, m.lx);
         MSB_REQUIRE(int64_t(ord.size()) == D, "row order size mismatch");
         std::vector<int32_t> tpos;
         std::vector<uint8_t> cpos;
@@ -51,7 +81,7 @@ static void build_hubbard(msb_op* op, const msb_model& m, int intermediate) {
         op->hdn16.upload(t16.data(), t16.size());
         if (D % 2 == 0 && D >= 2) {
             // targets moved to their shared-memory slots for the FP32 row-tiled apply
-            const RowLayout& lay = cached_row_layout(m.L, op->sec_dn, m.periodic != 0, kApplyThreads);
+            const RowLayout& lay = cached_row_layout(m.L, op->sec_dn, m.periodic != 0, kApplyThreads, m.lx);
             MSB_REQUIRE(int64_t(lay.perm.size()) == D, "row layout size mismatch");
             std::vector<uint16_t> tp(tpos.size());
             for (size_t i = 0; i < tpos.size(); ++i) {
@@ -90,14 +120,17 @@ static void build_hubbard(msb_op* op, const msb_model& m, int intermediate) {
         h.dsign = dn ? 1 : 0;
     }
     h.t = m.t; h.U = m.U; h.Uc = m.Uc;
+    h.hup2 = op->hup2.p; h.hdn2 = op->hdn2.p;
+    h.nup2 = op->nup2.p; h.ndn2 = op->ndn2.p;
+    h.t2 = m.tp;
     h.tf = float(m.t); h.Uf = float(m.U); h.Ucf = float(m.Uc);
-    h.core = intermediate ? m.core_site : -1;
+    h.core = intermediate == 1 ? m.core_site : -1;
     h.L = m.L;
     op->dim = h.Dup * h.Ddn;
     double nh = 0;
     for (uint8_t c : cu) nh += double(c) * double(h.Ddn);
     for (uint8_t c : cd) nh += double(c) * double(h.Dup);
-    op->offdiag = nh;
+    op->offdiag = nh + op->offdiag2;
 }
 
 static void build_csr(msb_op* op, int64_t n, const int64_t* rowptr, const int32_t* col,
@@ -196,7 +229,7 @@ extern "C" msb_status msb_op_create_hubbard(const msb_model* model, int intermed
         MSB_REQUIRE(model != nullptr && out != nullptr, "NULL argument");
         msb::require_device();
         auto op = std::make_unique<msb_op>();
-        msb::build_hubbard(op.get(), *model, intermediate ? 1 : 0);
+        msb::build_hubbard(op.get(), *model, intermediate);
         *out = op.release();
     });
 }

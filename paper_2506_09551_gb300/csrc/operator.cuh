@@ -75,7 +75,14 @@ struct HubView {
     const uint16_t* slot16; // shared-memory slot of each position (with hdn16p), or null
     const uint32_t* sup;   // occupation strings, rank order
     const uint32_t* sdn;
-    int usign, dsign;      // 1 if some up / down hop carries a negative sign (ring bond, (-1)^(N-1) = -1)
+    int usign, dsign;      // 1 if some up / down hop carries a negative sign (Jordan-Wigner string)
+    // diagonal bonds of a 2D cluster (hopping t2 = t'), same layout; null without them
+    int Wup2, Wdn2;
+    const int32_t* hup2;
+    const int32_t* hdn2;
+    const uint8_t* nup2;
+    const uint8_t* ndn2;
+    double t2;
     double t, U, Uc;
     int core;              // core-hole site, -1: none (plain H)
     int L;                 // sites
@@ -108,8 +115,25 @@ struct HubView {
             const V v = xrow[h >> 1];
             acc = (h & 1) ? vsub(acc, v) : vadd(acc, v);
         }
-        // H x = diag * x - t * sum(sign * x_neighbour)
-        return vaxpy(S(-t), acc, vscale(diag<S>(iu, id), xs));
+        // H x = diag * x - t * sum(sign * x_neighbour) - t2 * sum over the diagonal bonds
+        V out = vaxpy(S(-t), acc, vscale(diag<S>(iu, id), xs));
+        if (hup2) {
+            V acc2 = vzero(xs);
+            const int nu2 = __ldg(nup2 + iu);
+            for (int e = 0; e < nu2; ++e) {
+                const int32_t h = __ldg(hup2 + int64_t(e) * Dup + iu);
+                const V v = x[int64_t(h >> 1) * Ddn + id];
+                acc2 = (h & 1) ? vsub(acc2, v) : vadd(acc2, v);
+            }
+            const int nd2 = __ldg(ndn2 + id);
+            for (int e = 0; e < nd2; ++e) {
+                const int32_t h = __ldg(hdn2 + int64_t(e) * Ddn + id);
+                const V v = xrow[h >> 1];
+                acc2 = (h & 1) ? vsub(acc2, v) : vadd(acc2, v);
+            }
+            out = vaxpy(S(-t2), acc2, out);
+        }
+        return out;
     }
 
     template <typename V>
@@ -195,8 +219,8 @@ struct msb_op {
     msb_model model{};
     int intermediate = 0;
     int sec_up = 0, sec_dn = 0;  // electrons of this operator's sector
-    msb::DevBuf<int32_t> hup, hdn;
-    msb::DevBuf<uint8_t> nup, ndn;
+    msb::DevBuf<int32_t> hup, hdn, hup2, hdn2;
+    msb::DevBuf<uint8_t> nup, ndn, nup2, ndn2;
     msb::DevBuf<uint16_t> hdn16, hdn16p, slot16, dpos;
     msb::DevBuf<uint8_t> ndnp;
     msb::DevBuf<uint32_t> sdnp;
@@ -214,6 +238,7 @@ struct msb_op {
     msb::SumView sum{};
     int device = 0;
     double offdiag = 0;          // off-diagonal entries (hops, or CSR nonzeros)
+    double offdiag2 = 0;         // of them, the diagonal-bond hops of a 2D cluster
 
     // Floating-point operations of one application (A x)[all s] on complex
     // vectors: two adds per hop plus the diagonal and hopping scale (Hubbard),
@@ -237,19 +262,30 @@ struct RowLayout {
 };
 RowLayout row_layout(const std::vector<int32_t>& table, const std::vector<uint8_t>& count, int64_t D, int W,
                      int threads);
-const RowLayout& cached_row_layout(int L, int n, bool periodic, int threads);
+const RowLayout& cached_row_layout(int L, int n, bool periodic, int threads, int lx = 0);
 // Continued-fraction row order (basis.cu): order[p] = down state at position p
 // of a row, sorted by hop count; the rank-space table rewritten to positions.
 std::vector<uint16_t> row_order(const std::vector<uint8_t>& count);
-const std::vector<uint16_t>& cached_row_order(int L, int n, bool periodic);
+const std::vector<uint16_t>& cached_row_order(int L, int n, bool periodic, int lx = 0);
 void table_in_row_order(const std::vector<int32_t>& table, const std::vector<uint8_t>& count, int64_t D, int W,
                         const std::vector<uint16_t>& ord, std::vector<int32_t>& tpos, std::vector<uint8_t>& cpos);
 // Host-side sector enumeration and hopping tables (basis.cu).
 std::vector<uint32_t> sector_states(int L, int n);
-// ELL hop table [W][D] with entries (target << 1) | neg, -1 empty; counts per state.
+// A bond (i, j) of the lattice; cls 0: hopping t, cls 1: the diagonal hopping t'.
+struct Bond { int i, j, cls; };
+// Bonds of the chain (lx = 0) or of the periodic lx x (L / lx) cluster (diagonal
+// bonds only with diag).
+std::vector<Bond> lattice_bonds(int L, bool periodic, int lx, bool diag);
+// ELL hop table [W][D] of the class-cls bonds, entries (target << 1) | neg, -1
+// empty; counts per state.
+void hop_table_bonds(const std::vector<Bond>& bonds, int cls, int L, int n, const std::vector<uint32_t>& states,
+                     std::vector<int32_t>& table, std::vector<uint8_t>& count, int& W);
+// The nearest-neighbour table of the chain or 2D cluster.
 void hop_table(int L, int n, bool periodic, const std::vector<uint32_t>& states,
-               std::vector<int32_t>& table, std::vector<uint8_t>& count, int& W);
+               std::vector<int32_t>& table, std::vector<uint8_t>& count, int& W, int lx = 0);
 void validate_model(const msb_model& m);
+// Electron counts of a model's sector: 0 ground, 1 intermediate, 2 final (operator.cu).
+void model_sector(const msb_model& m, int which, int& n_up, int& n_dn);
 // y = (A + c0) x for nvec columns (operator.cu).
 void op_apply(msb_op* op, double2 c0, const void* x, void* y, int nvec, msb_precision prec,
               cudaStream_t st);

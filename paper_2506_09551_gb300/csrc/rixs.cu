@@ -101,6 +101,70 @@ static void launch_rowmap(const VS* x, VD* y, const std::vector<int32_t>& map, i
     ++launches;
 }
 
+// y[row, dst_col] = sign * x[row, src_col] for every column of a block: the
+// down-spin creation / annihilation operators, which act inside a row.  Map
+// entry per destination down state (src_col << 1) | neg, or -1 for zero; every
+// entry also takes (-1)^{n_up} (neg_all), the up orbitals the operator passes in
+// the Jordan-Wigner order.
+template <typename VS, typename VD>
+__global__ void __launch_bounds__(256) k_colmap(const VS* __restrict__ x, VD* __restrict__ y,
+                                                const int32_t* __restrict__ map, int64_t Dup, int64_t Dsrc,
+                                                int64_t Ddst, int neg_all, int64_t ld_x, int64_t ld_y) {
+    const int64_t n = Dup * Ddst;
+    const VS* __restrict__ xc = x + int64_t(blockIdx.y) * ld_x;
+    VD* __restrict__ yc = y + int64_t(blockIdx.y) * ld_y;
+    for (int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < n; s += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t u = s / Ddst, d = s - u * Ddst;
+        const int32_t m = __ldg(map + d);
+        VD out = vzero(VD{});
+        if (m >= 0) {
+            const VS v = xc[u * Dsrc + (m >> 1)];
+            if constexpr (is_cplx_v<VS>) {
+                out = mk(scalar_t<VD>(v.x), scalar_t<VD>(v.y));
+            } else {
+                out = mk(scalar_t<VD>(v), scalar_t<VD>(0));
+            }
+            if ((m & 1) ^ neg_all) out = vsub(vzero(VD{}), out);
+        }
+        yc[s] = out;
+    }
+}
+
+template <typename VS, typename VD>
+static void launch_colmap(const VS* x, VD* y, const std::vector<int32_t>& map, int64_t Dup, int64_t Dsrc, int neg_all,
+                          int64_t ld_x, int64_t ld_y, int nvec, cudaStream_t st, int64_t& launches) {
+    DevBuf<int32_t> dmap(map.size());
+    dmap.upload(map.data(), map.size(), st);
+    const int64_t Ddst = int64_t(map.size());
+    const int64_t n = Dup * Ddst;
+    {
+        ProfScope ps("sector_map", st, double(nvec) * n * (sizeof(VS) + sizeof(VD)), 0);
+        k_colmap<VS, VD><<<dim3(grid_for(n, 256, 8), nvec), 256, 0, st>>>(x, y, dmap.p, Dup, Dsrc, Ddst, neg_all, ld_x,
+                                                                           ld_y);
+    }
+    MSB_LAUNCH_CHECK();
+    MSB_CUDA(cudaStreamSynchronize(st));   // dmap is freed on return
+    ++launches;
+}
+
+// y = c^dag_{j,spin} x (create) or c_{j,spin} x for nvec vectors of the (nu, nd) sector
+// (vector strides ld_x, ld_y): up spin maps rows, down spin maps the columns of a row.
+template <typename VS, typename VD>
+static void launch_sector_op(const VS* x, VD* y, int L, int nu, int nd, int j, int spin, bool create, int64_t ld_x,
+                             int64_t ld_y, int nvec, cudaStream_t st, int64_t& launches) {
+    if (spin == 0) {
+        MSB_REQUIRE(create ? nu + 1 <= L : nu >= 1, "no up electron to create / annihilate");
+        auto map = create ? cdag_rowmap(L, nu, j) : c_rowmap(L, nu - 1, j);
+        const int64_t Ddn = int64_t(sector_states(L, nd).size());
+        launch_rowmap(x, y, map, Ddn, ld_x, ld_y, nvec, st, launches);
+    } else {
+        MSB_REQUIRE(create ? nd + 1 <= L : nd >= 1, "no down electron to create / annihilate");
+        auto map = create ? cdag_rowmap(L, nd, j) : c_rowmap(L, nd - 1, j);
+        const int64_t Dup = int64_t(sector_states(L, nu).size()), Dsrc = int64_t(sector_states(L, nd).size());
+        launch_colmap(x, y, map, Dup, Dsrc, nu & 1, ld_x, ld_y, nvec, st, launches);
+    }
+}
+
 static void apply_sector_map(const msb_model& m, int site, bool create, const void* x, void* y, int nvec,
                              msb_precision prec, cudaStream_t st) {
     validate_model(m);
@@ -124,29 +188,34 @@ static void apply_sector_map(const msb_model& m, int site, bool create, const vo
 // ---------------------------------------------------------------------------
 // Steps 3-5 of the map for one core site (m.core_site): E = O2|G>, the
 // multi-shift solve on H' of that site, and phi_k = O1 Psi_k written to Phi
-// (n_in vectors of the ground sector, precision of prm).  Returns the solve status.
-static msb_status solve_site(msb_op* opHp, const msb_op* opH, const msb_model& m, const msb_map_params& prm,
-                             const double* G, double E_G, const double* w_in, int n_in, char* Phi,
-                             msb_solve_info& info, cudaStream_t st, int64_t& launches) {
-    const int64_t D = opH->dim, Dp = opHp->dim, Ddn = opH->hub.Ddn;
+// (n_in vectors of the final sector, precision of prm).  Returns the solve status.
+// O2 = c^dag_{j,o2_spin}, O1 = c_{j,o1_spin}.  With an up-spin O1 only the rows of
+// the intermediate sector that O1 reads (site j up-occupied) are carried per shift,
+// since the per-shift update is elementwise; a down-spin O1 acts inside every row.
+static msb_status solve_site(msb_op* opHp, const msb_op* opH, const msb_op* opHf, const msb_model& m,
+                             const msb_map_params& prm, const double* G, double E_G, const double* w_in, int n_in,
+                             char* Phi, msb_solve_info& info, cudaStream_t st, int64_t& launches) {
+    const int64_t D = opH->dim, Dp = opHp->dim, Df = opHf->dim;
+    const int j = m.core_site;
+    int nu_i = 0, nd_i = 0;
+    model_sector(m, 1, nu_i, nd_i);
+    const int64_t Ddn_i = opHp->hub.Ddn;
     const size_t csz = prm.precision == MSB_FP64 ? sizeof(double2) : sizeof(float2);
     DevBuf<char> Ebuf(size_t(Dp) * csz);
-    {
-        auto map = cdag_rowmap(m.L, m.n_up, m.core_site);
-        if (prm.precision == MSB_FP64)
-            launch_rowmap(G, (double2*)Ebuf.p, map, Ddn, D, Dp, 1, st, launches);
-        else
-            launch_rowmap(G, (float2*)Ebuf.p, map, Ddn, D, Dp, 1, st, launches);
-    }
-    // rows of the intermediate sector that O1 reads (site j up-occupied)
-    const auto up_hi = sector_states(m.L, m.n_up + 1);
+    if (prm.precision == MSB_FP64)
+        launch_sector_op(G, (double2*)Ebuf.p, m.L, m.n_up, m.n_dn, j, m.o2_spin, true, D, Dp, 1, st, launches);
+    else
+        launch_sector_op(G, (float2*)Ebuf.p, m.L, m.n_up, m.n_dn, j, m.o2_spin, true, D, Dp, 1, st, launches);
+    // rows of the intermediate sector that an up-spin O1 reads (site j up-occupied)
+    const auto up_hi = sector_states(m.L, nu_i);
     std::vector<int32_t> rows;
     std::vector<int32_t> pos(up_hi.size(), -1);
-    for (size_t r = 0; r < up_hi.size(); ++r)
-        if ((up_hi[r] >> m.core_site) & 1u) { pos[r] = int32_t(rows.size()); rows.push_back(int32_t(r)); }
+    if (m.o1_spin == 0)
+        for (size_t r = 0; r < up_hi.size(); ++r)
+            if ((up_hi[r] >> j) & 1u) { pos[r] = int32_t(rows.size()); rows.push_back(int32_t(r)); }
     DevBuf<int32_t> drows(rows.size());
-    drows.upload(rows.data(), rows.size(), st);
-    const int64_t n_out = int64_t(rows.size()) * Ddn;
+    if (!rows.empty()) drows.upload(rows.data(), rows.size(), st);
+    const int64_t n_out = m.o1_spin == 0 ? int64_t(rows.size()) * Ddn_i : Dp;
     // seed and shifts
     int s0 = prm.seed_index;
     if (s0 < 0) {
@@ -159,8 +228,8 @@ static msb_status solve_site(msb_op* opHp, const msb_op* opH, const msb_model& m
     pr.ns = n_in;
     pr.b = Ebuf.p;
     pr.n_out = n_out;
-    pr.rows = drows.p;
-    pr.rowlen = Ddn;
+    pr.rows = m.o1_spin == 0 ? drows.p : nullptr;
+    pr.rowlen = Ddn_i;
     pr.c0 = make_double2(-E_G - w_in[s0], -prm.Gamma);
     pr.tol = prm.solve_tol;
     pr.maxit = prm.maxit;
@@ -182,22 +251,30 @@ static msb_status solve_site(msb_op* opHp, const msb_op* opH, const msb_model& m
     info.matvecs += sr.iterations;
     if (sr.status != MSB_OK && sr.status != MSB_EMAXITER) fail(sr.status, "multi-shift solve failed");
     Ebuf.release();
-    // phi_k = O1 Psi_k from the carried rows
-    std::vector<int32_t> omap(opH->hub.Dup, -1);
-    {
-        const auto up_lo = sector_states(m.L, m.n_up);
+    // phi_k = O1 Psi_k
+    if (m.o1_spin == 0) {
+        std::vector<int32_t> omap(size_t(Df / Ddn_i), -1);
+        const auto up_lo = sector_states(m.L, nu_i - 1);
+        MSB_REQUIRE(int64_t(up_lo.size()) * Ddn_i == Df, "final sector size mismatch");
         auto rhi = rank_table(up_hi, m.L);
         for (size_t r = 0; r < up_lo.size(); ++r) {
             const uint32_t u = up_lo[r];
-            if ((u >> m.core_site) & 1u) continue;
-            const int32_t src = pos[rhi[u | (1u << m.core_site)]];
-            omap[r] = (src << 1) | jw_sign_below(u, m.core_site);
+            if ((u >> j) & 1u) continue;
+            const int32_t src = pos[rhi[u | (1u << j)]];
+            omap[r] = (src << 1) | jw_sign_below(u, j);
         }
+        if (prm.precision == MSB_FP64)
+            launch_rowmap((const double2*)Xsub.p, (double2*)Phi, omap, Ddn_i, n_out, Df, n_in, st, launches);
+        else
+            launch_rowmap((const float2*)Xsub.p, (float2*)Phi, omap, Ddn_i, n_out, Df, n_in, st, launches);
+    } else {
+        if (prm.precision == MSB_FP64)
+            launch_sector_op((const double2*)Xsub.p, (double2*)Phi, m.L, nu_i, nd_i, j, 1, false, Dp, Df, n_in, st,
+                             launches);
+        else
+            launch_sector_op((const float2*)Xsub.p, (float2*)Phi, m.L, nu_i, nd_i, j, 1, false, Dp, Df, n_in, st,
+                             launches);
     }
-    if (prm.precision == MSB_FP64)
-        launch_rowmap((const double2*)Xsub.p, (double2*)Phi, omap, Ddn, n_out, D, n_in, st, launches);
-    else
-        launch_rowmap((const float2*)Xsub.p, (float2*)Phi, omap, Ddn, n_out, D, n_in, st, launches);
     return sr.status;
 }
 
@@ -208,7 +285,6 @@ void rixs_map_core(msb_op* opH, msb_op* opHp, const msb_model& m, const msb_map_
 void rixs_map(const msb_model& m, const msb_map_params& prm, const double* G_in, double E_G_in, const double* w_in,
               int n_in, const double* w, int n_w, double* I_out, msb_solve_info& info, cudaStream_t st) {
     validate_model(m);
-    MSB_REQUIRE(m.n_up + 1 <= m.L, "the intermediate sector needs n_up + 1 <= L");
     std::unique_ptr<msb_op> opH, opHp;
     {
         msb_op* a = nullptr;
@@ -226,7 +302,6 @@ void rixs_map_core(msb_op* opH_, msb_op* opHp_, const msb_model& m, const msb_ma
                    double E_G_in, const double* w_in, int n_in, const double* w, int n_w, double* I_out, bool I_dev,
                    msb_solve_info& info, cudaStream_t st, int64_t launches_so_far) {
     validate_model(m);
-    MSB_REQUIRE(m.n_up + 1 <= m.L, "the intermediate sector needs n_up + 1 <= L");
     MSB_REQUIRE(n_in >= 1 && n_in <= kMaxShifts, "n_in must be in 1..4096");
     MSB_REQUIRE(n_w >= 1, "n_w must be >= 1");
     MSB_REQUIRE(w_in && w && I_out, "NULL argument");
@@ -260,17 +335,28 @@ void rixs_map_core(msb_op* opH_, msb_op* opHp_, const msb_model& m, const msb_ma
     info.E_G = E_G;
     info.seconds_ground_state = secs(t0);
 
+    // the final sector: the ground sector in the spin-conserving channel
+    std::unique_ptr<msb_op> opHf_own;
+    msb_op* opHf = opH.get();
+    if (m.o1_spin != m.o2_spin) {
+        msb_op* a = nullptr;
+        const msb_status s1 = msb_op_create_hubbard(&m, 2, &a);
+        if (s1 != MSB_OK) fail(s1, msb_last_error());
+        opHf_own.reset(a);
+        opHf = a;
+    }
     // E = O2 |G>, the multi-shift solve, phi = O1 Psi
     t0 = std::chrono::steady_clock::now();
     const size_t csz = prm.precision == MSB_FP64 ? sizeof(double2) : sizeof(float2);
-    DevBuf<char> Phi(size_t(n_in) * D * csz);
-    const msb_status sst = solve_site(opHp.get(), opH.get(), m, prm, G, E_G, w_in, n_in, Phi.p, info, st, launches);
+    DevBuf<char> Phi(size_t(n_in) * opHf->dim * csz);
+    const msb_status sst =
+        solve_site(opHp.get(), opH.get(), opHf, m, prm, G, E_G, w_in, n_in, Phi.p, info, st, launches);
     info.seconds_solve = secs(t0);
 
-    // second step
+    // second step, on the final sector's H
     t0 = std::chrono::steady_clock::now();
     CFResult cr;
-    continued_fraction(opH.get(), Phi.p, n_in, E_G, w, n_w, prm.eta, prm.cf_tol, prm.cf_check, prm.cf_maxdepth,
+    continued_fraction(opHf, Phi.p, n_in, E_G, w, n_w, prm.eta, prm.cf_tol, prm.cf_check, prm.cf_maxdepth,
                        prm.precision, I_out, cr, st, I_dev);
     launches += cr.launches;
     info.matvecs += cr.matvecs;
@@ -464,6 +550,7 @@ static void rixs_map_sites_impl(const msb_model& m, const msb_map_params& prm, c
                                 msb_solve_info& info, cudaStream_t st, const double* qs = nullptr,
                                 int n_q = 0) {
     validate_model(m);
+    MSB_REQUIRE(m.o2_spin == 0 && m.o1_spin == 0, "the site batch supports the up-spin channel");
     MSB_REQUIRE(sites != nullptr && n_sites >= 1, "need at least one site");
     MSB_REQUIRE(n_in >= 1 && n_in <= kMaxShifts && int64_t(n_sites) * n_in <= 65535,
                 "n_sites * n_in must be at most 65535 (and n_in at most 4096)");
@@ -561,6 +648,7 @@ static void rixs_map_clusters_impl(const msb_model* models, int nc, const msb_ma
     MSB_REQUIRE(prm.precision == MSB_FP64 || prm.precision == MSB_FP32_MIXED, "unknown precision");
     for (int c = 0; c < nc; ++c) {
         validate_model(models[c]);
+        MSB_REQUIRE(models[c].o2_spin == 0 && models[c].o1_spin == 0, "the cluster batch supports the up-spin channel");
         MSB_REQUIRE(models[c].n_up + 1 <= models[c].L, "the intermediate sector needs n_up + 1 <= L");
         MSB_REQUIRE(models[c].core_site >= 0 && models[c].core_site < models[c].L, "core_site out of range");
     }
@@ -718,7 +806,8 @@ static void rixs_map_clusters_impl(const msb_model* models, int nc, const msb_ma
 
 static bool same_model(const msb_model& a, const msb_model& b) {
     return a.L == b.L && a.n_up == b.n_up && a.n_dn == b.n_dn && a.periodic == b.periodic && a.t == b.t &&
-           a.U == b.U && a.Uc == b.Uc && a.core_site == b.core_site;
+           a.U == b.U && a.Uc == b.Uc && a.core_site == b.core_site && a.o2_spin == b.o2_spin &&
+           a.o1_spin == b.o1_spin && a.lx == b.lx && a.tp == b.tp;
 }
 
 extern "C" msb_status msb_rixs_map_ops(msb_op* H, msb_op* Hp, const msb_map_params* params, const double* G,
@@ -728,8 +817,8 @@ extern "C" msb_status msb_rixs_map_ops(msb_op* H, msb_op* Hp, const msb_map_para
     return msb::guard("msb_rixs_map_ops", [&] {
         msb::require_device();
         MSB_REQUIRE(H != nullptr && Hp != nullptr && params != nullptr, "NULL argument");
-        MSB_REQUIRE(H->kind == 0 && Hp->kind == 0 && !H->intermediate && Hp->intermediate,
-                    "H and Hp must be the Hubbard operators of one model (intermediate 0 and 1)");
+        MSB_REQUIRE(H->kind == 0 && Hp->kind == 0 && H->intermediate == 0 && Hp->intermediate == 1,
+                    "H and Hp must be the Hubbard operators of one model (sectors 0 and 1)");
         MSB_REQUIRE(same_model(H->model, Hp->model), "H and Hp belong to different models");
         msb::g_alloc_bytes = 0;
         msb_solve_info local{};

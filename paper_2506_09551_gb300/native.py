@@ -24,7 +24,8 @@ class msb_complex(C.Structure):
 
 class msb_model(C.Structure):
     _fields_ = [("L", C.c_int), ("n_up", C.c_int), ("n_dn", C.c_int), ("periodic", C.c_int),
-                ("t", C.c_double), ("U", C.c_double), ("Uc", C.c_double), ("core_site", C.c_int)]
+                ("t", C.c_double), ("U", C.c_double), ("Uc", C.c_double), ("core_site", C.c_int),
+                ("o2_spin", C.c_int), ("o1_spin", C.c_int), ("lx", C.c_int), ("tp", C.c_double)]
 
 
 class msb_map_params(C.Structure):
