@@ -81,6 +81,12 @@ typedef struct {
                          site x + lx y, lx >= 3 and L / lx >= 3                  */
     double tp;        /* diagonal (next-nearest-neighbour) hopping t' of a 2D
                          cluster; bonds (x,y)-(x+1,y+1) and (x,y)-(x-1,y+1)      */
+    double flux;      /* magnetic flux through a ring (Peierls phases): the hop of
+                         an electron from site i to i + 1 carries exp(i flux / L),
+                         the reverse hop exp(-i flux / L).  Nonzero makes H
+                         complex Hermitian: only the dual solver
+                         (msb_multishift_bicg_dual_solve) and msb_op_apply take
+                         such an operator.  Chain only (lx = 0).                 */
 } msb_model;
 
 /* Parameters of the whole map (Eqs. 1-2). */
@@ -285,12 +291,32 @@ msb_status msb_ground_state_noalloc(msb_op *H, double tol, int maxit, const doub
  * p^(k), x^(k) are advanced once every `block` iterations from the stored seed
  * residuals, with coefficients from the same recurrences.
  * Returns MSB_EMAXITER (results still written) if a shift did not converge
- * within maxit, MSB_EBREAKDOWN / MSB_ENONFINITE on a failed recurrence. */
+ * within maxit, MSB_EBREAKDOWN / MSB_ENONFINITE on a failed recurrence,
+ * MSB_EINVAL for an operator with Peierls phases (not complex symmetric: use
+ * msb_multishift_bicg_dual_solve). */
 msb_status msb_multishift_bicg_solve(msb_op *A, msb_complex c0, const void *b,
                                      const msb_complex *shifts, int n_shifts, double tol,
                                      int maxit, int block, msb_precision prec, void *x,
                                      int *iters, double *resid, int *converged,
                                      msb_solve_info *info, void *stream);
+
+/* The same multi-shift solve for an operator A that is Hermitian but not real
+ * symmetric (a Hubbard ring with Peierls phases, msb_model.flux != 0), where
+ * A + c0 is not complex symmetric and the bilinear form no longer makes the
+ * residuals biorthogonal.  Dual-space BiCG (App. A): a second recurrence in the
+ * space of (A + c0)^dagger = A + conj(c0), with dual residual r~ (r~_0 = b) and
+ * direction p~, and Hermitian products: alpha = <r~|r> / <p~|A p>,
+ * r~ <- r~ - conj(alpha) (A + conj(c0)) p~, p~ <- r~ + conj(beta) p~.  Two operator
+ * applications per iteration (info->matvecs = 2 * iterations).  The shifted
+ * residuals stay collinear with the seed's (App. B), so the per-shift zeta /
+ * alpha / beta recurrences and the fused per-shift update are those of
+ * msb_multishift_bicg_solve.  Arguments, outputs and errors as that call; it
+ * also accepts a real symmetric A (then it converges to the same solutions). */
+msb_status msb_multishift_bicg_dual_solve(msb_op *A, msb_complex c0, const void *b,
+                                          const msb_complex *shifts, int n_shifts, double tol,
+                                          int maxit, int block, msb_precision prec, void *x,
+                                          int *iters, double *resid, int *converged,
+                                          msb_solve_info *info, void *stream);
 
 /* Adaptive reseeding (App. E, Fig. 5) around the solve above.  Solves
  * (A + c0 I - s_k I) x_k = b for every shift, first from the seed system

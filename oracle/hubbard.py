@@ -180,15 +180,20 @@ def hop_term(sec: Sector, i: int, j: int, spin: int):
 
 
 def hamiltonian(sec: Sector, t: float, U: float, Uc: float = 0.0, core_site: int | None = None,
-                periodic: bool = True, bond_list=None) -> sp.csr_matrix:
+                periodic: bool = True, bond_list=None, flux: float = 0.0) -> sp.csr_matrix:
     """H of Eq. (9) on `sec`, plus -Uc (n_{j,up} + n_{j,dn}) of Eq. (10) when core_site is set.
-    bond_list: (i, j, t_ij) bonds (cluster_bonds); default the chain's bonds with hopping t."""
+    bond_list: (i, j, t_ij) bonds (cluster_bonds); default the chain's bonds with hopping t.
+    flux: a magnetic flux through the ring (Peierls phases): the hop of an electron from
+    i to j = i + 1 (mod L) carries exp(+i flux / L), the reverse hop exp(-i flux / L),
+    which makes H complex Hermitian (chain bonds only)."""
     R, C, V = [], [], []
+    theta = flux / sec.L
     for (i, j, tij) in (bond_list if bond_list is not None else [(i, j, t) for (i, j) in bonds(sec.L, periodic)]):
         for s in (0, 1):
-            for (a, b) in ((i, j), (j, i)):        # c^dag_b c_a and its h.c.
+            for (a, b), ph in (((i, j), theta), ((j, i), -theta)):   # c^dag_b c_a and its h.c.
                 r, c, v = hop_term(sec, a, b, s)
-                R.append(r); C.append(c); V.append(-tij * v)
+                amp = -tij * (np.exp(1j * ph) if flux != 0.0 else 1.0)
+                R.append(r); C.append(c); V.append(amp * v)
     diag = np.zeros(sec.dim)
     for i in range(sec.L):
         diag += U * (sec.occupation(i, 0) * sec.occupation(i, 1))

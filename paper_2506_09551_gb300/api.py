@@ -34,11 +34,12 @@ def cdtype(prec: int) -> torch.dtype:
 
 
 def model(L, n_up, n_dn, t=1.0, U=8.0, Uc=4.0, core_site=0, periodic=True, o2_spin=0, o1_spin=None, lx=0,
-          tp=0.0) -> N.msb_model:
+          tp=0.0, flux=0.0) -> N.msb_model:
     """A Hubbard chain (lx = 0) or periodic lx x (L / lx) cluster with diagonal hopping tp, and
-    the RIXS channel O2 = c^dag_{j,o2_spin}, O1 = c_{j,o1_spin} (o1_spin defaults to o2_spin)."""
+    the RIXS channel O2 = c^dag_{j,o2_spin}, O1 = c_{j,o1_spin} (o1_spin defaults to o2_spin);
+    flux: Peierls phases on a ring (complex Hermitian H)."""
     o1 = o2_spin if o1_spin is None else o1_spin
-    return N.msb_model(L, n_up, n_dn, 1 if periodic else 0, t, U, Uc, core_site, o2_spin, o1, lx, tp)
+    return N.msb_model(L, n_up, n_dn, 1 if periodic else 0, t, U, Uc, core_site, o2_spin, o1, lx, tp, flux)
 
 
 def map_params(**kw) -> N.msb_map_params:
@@ -179,8 +180,9 @@ class Operator:
         return E.value, g, res.value
 
     def multishift_solve(self, b: torch.Tensor, shifts, c0: complex = 0.0, tol: float = 1e-10, maxit: int = 5000,
-                         block: int = 0, prec: int = FP64, allow_status=()):
-        """x_k = (A + c0 - s_k)^{-1} b for every shift.  Returns (x, per-shift dict, info dict, status)."""
+                         block: int = 0, prec: int = FP64, allow_status=(), dual: bool = False):
+        """x_k = (A + c0 - s_k)^{-1} b for every shift.  Returns (x, per-shift dict, info dict, status).
+        dual: the dual-space form for a Hermitian, not real symmetric, A (Peierls phases)."""
         shifts = np.asarray(shifts, dtype=np.complex128)
         ns = len(shifts)
         sh = (N.msb_complex * ns)(*[N.msb_complex(s.real, s.imag) for s in shifts])
@@ -190,7 +192,8 @@ class Operator:
         conv = np.zeros(ns, dtype=np.int32)
         info = N.msb_solve_info()
         c0 = complex(c0)
-        st = N.load().msb_multishift_bicg_solve(
+        fn = N.load().msb_multishift_bicg_dual_solve if dual else N.load().msb_multishift_bicg_solve
+        st = fn(
             self.h, N.msb_complex(c0.real, c0.imag), _ptr(b.to(cdtype(prec)).contiguous()), sh, ns, tol, maxit,
             block, prec, _ptr(x), iters.ctypes.data_as(C.POINTER(C.c_int)),
             resid.ctypes.data_as(C.POINTER(C.c_double)), conv.ctypes.data_as(C.POINTER(C.c_int)), C.byref(info),

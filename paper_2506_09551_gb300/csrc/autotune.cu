@@ -179,6 +179,8 @@ extern "C" msb_status msb_autotune(const msb_model* model, msb_precision prec, i
         msb::require_device();
         MSB_REQUIRE(model != nullptr, "model is NULL");
         msb::validate_model(*model);
+        MSB_REQUIRE(model->flux == 0.0, "the autotuner times the real-H map path (no flux)");
+        MSB_REQUIRE(model->o2_spin == 0 && model->o1_spin == 0, "the autotuner times the up-spin channel");
         MSB_REQUIRE(model->n_up + 1 <= model->L, "the intermediate sector needs n_up + 1 <= L");
         MSB_REQUIRE(prec == MSB_FP64 || prec == MSB_FP32_MIXED, "unknown precision");
         MSB_REQUIRE(n_in >= 1 && n_in <= msb::kMaxShifts, "n_in must be in 1..4096");

@@ -57,7 +57,7 @@ std::vector<Bond> lattice_bonds(int L, bool periodic, int lx, bool diag) {
 // between a and b, (-1)^(their number).  (On the ring this is -1 only for the bond
 // L-1 -- 0 with an even electron count: (-1)^(N - 1).)
 void hop_table_bonds(const std::vector<Bond>& bonds, int cls, int L, int n, const std::vector<uint32_t>& states,
-                     std::vector<int32_t>& table, std::vector<uint8_t>& count, int& W) {
+                     std::vector<int32_t>& table, std::vector<uint8_t>& count, int& W, std::vector<uint8_t>* dir) {
     (void)n;
     const int64_t D = int64_t(states.size());
     std::vector<int32_t> rank(size_t(1) << L, -1);
@@ -69,6 +69,7 @@ void hop_table_bonds(const std::vector<Bond>& bonds, int cls, int L, int n, cons
     MSB_REQUIRE(W <= 255, "too many bonds for the hop table");
     table.assign(size_t(W) * D, -1);
     count.assign(size_t(D), 0);
+    if (dir) dir->assign(size_t(W) * D, 0);
     for (int64_t k = 0; k < D; ++k) {
         const uint32_t s = states[k];
         int c = 0;
@@ -80,6 +81,9 @@ void hop_table_bonds(const std::vector<Bond>& bonds, int cls, int L, int n, cons
             const bool neg = __builtin_popcount(s & between) & 1;
             const uint32_t tgt = s ^ (1u << b.i) ^ (1u << b.j);
             table[size_t(c) * D + k] = (rank[tgt] << 1) | (neg ? 1 : 0);
+            // <s|H|target>: the electron moves from its site in the target to its site in s,
+            // i -> j (the bond's direction) when s holds it on j
+            if (dir) (*dir)[size_t(c) * D + k] = uint8_t(bj);
             ++c;
         }
         count[k] = uint8_t(c);
@@ -87,8 +91,8 @@ void hop_table_bonds(const std::vector<Bond>& bonds, int cls, int L, int n, cons
 }
 
 void hop_table(int L, int n, bool periodic, const std::vector<uint32_t>& states,
-               std::vector<int32_t>& table, std::vector<uint8_t>& count, int& W, int lx) {
-    hop_table_bonds(lattice_bonds(L, periodic, lx, false), 0, L, n, states, table, count, W);
+               std::vector<int32_t>& table, std::vector<uint8_t>& count, int& W, int lx, std::vector<uint8_t>* dir) {
+    hop_table_bonds(lattice_bonds(L, periodic, lx, false), 0, L, n, states, table, count, W, dir);
 }
 
 // ---------------------------------------------------------------------------
@@ -304,6 +308,7 @@ void validate_model(const msb_model& m) {
     MSB_REQUIRE(m.lx == 0 || (m.lx >= 3 && m.L % m.lx == 0 && m.L / m.lx >= 3),
                 "a 2D cluster needs lx >= 3 dividing L with L / lx >= 3");
     MSB_REQUIRE(std::isfinite(m.tp) && (m.tp == 0.0 || m.lx > 0), "tp needs a 2D cluster (lx > 0)");
+    MSB_REQUIRE(std::isfinite(m.flux) && (m.flux == 0.0 || m.lx == 0), "a flux needs a chain (lx = 0)");
 }
 
 }  // namespace msb

@@ -91,6 +91,13 @@ __device__ __forceinline__ void norm_acc_df(float2 v, DF4& a) {
     df_add_prod(a.nh, a.nl, v.x, v.x);
     df_add_prod(a.nh, a.nl, v.y, v.y);
 }
+// Compensated Hermitian product term conj(u) * v (FP32 vectors) into a DF4.
+__device__ __forceinline__ void her_acc_df(float2 u, float2 v, DF4& a) {
+    df_add_prod(a.rh, a.rl, u.x, v.x);
+    df_add_prod(a.rh, a.rl, u.y, v.y);
+    df_add_prod(a.ih, a.il, u.x, v.y);
+    df_add_prod(a.ih, a.il, -u.y, v.x);
+}
 // Hermitian product term conj(u) * v accumulated into (re, im).
 __device__ __forceinline__ void her_acc(double2 u, double2 v, double& re, double& im) {
     re = fma(u.x, v.x, fma(u.y, v.y, re));

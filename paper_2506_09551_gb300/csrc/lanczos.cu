@@ -400,6 +400,7 @@ void ground_state(msb_op* H, double tol, int maxit, const double* start, double*
     MSB_REQUIRE(maxit >= 2, "maxit must be >= 2");
     MSB_REQUIRE(tol > 0, "tol must be > 0");
     MSB_REQUIRE(H->kind != 2, "a direct sum has no single ground state: take each part's");
+    MSB_REQUIRE(!op_has_flux(H), "the ground state takes a real symmetric H (no flux)");
     if (H->kind == 0) ground_state_impl(H, H->hub, H->dim, tol, maxit, start, g, out, st);
     else ground_state_impl(H, H->csr, H->dim, tol, maxit, start, g, out, st);
     prof_collect();
@@ -1372,6 +1373,7 @@ void continued_fraction(msb_op* H, const void* phi, int n_vec, double E0, const 
     MSB_REQUIRE(H != nullptr && phi != nullptr, "NULL argument");
     cf_check_args(n_vec, w, n_w, eta, cf_check, cf_maxdepth, I_out);
     MSB_REQUIRE(H->kind != 2, "the continued fraction of a direct sum mixes its parts: use one part per column");
+    MSB_REQUIRE(!op_has_flux(H), "the continued fraction takes a real symmetric H (no flux)");
     CFColumns P;
     P.phi = phi;
     P.ldphi = H->dim;
@@ -1511,6 +1513,7 @@ extern "C" msb_status msb_ground_state_noalloc(msb_op* H, double tol, int maxit,
         MSB_CUDA(cudaGetDevice(&dev));
         MSB_REQUIRE(dev == H->device, "the operator was created on another device");
         MSB_REQUIRE(H->kind != 2, "a direct sum has no single ground state: take each part's");
+        MSB_REQUIRE(!msb::op_has_flux(H), "the ground state takes a real symmetric H (no flux)");
         cudaStream_t st = (cudaStream_t)stream;
         msb::GroundResult r;
         if (H->kind == 0) msb::ground_state_noalloc_impl(H, H->hub, H->dim, tol, maxit, start, g, r, st);

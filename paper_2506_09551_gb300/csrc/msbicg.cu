@@ -78,10 +78,12 @@ struct SeedState {
 // ---------------------------------------------------------------------------
 
 // v = A p (A = op + c0), partial mu = (p, v).
+// Dual form (pt != null, App. A): mu = <p~|v> (Hermitian) instead of (p, v).
 template <class View, typename V>
 __global__ void __launch_bounds__(256) k_mvm_dot(View op, const V* __restrict__ p, V* __restrict__ v,
                                                  int64_t n, double c0r, double c0i,
-                                                 const SeedState* __restrict__ st, double* part) {
+                                                 const SeedState* __restrict__ st, double* part,
+                                                 const V* __restrict__ pt) {
     if (st->done) return;
     __shared__ double sm[2 * 32];
     double acc[2] = {0.0, 0.0};
@@ -92,14 +94,30 @@ __global__ void __launch_bounds__(256) k_mvm_dot(View op, const V* __restrict__ 
         const V h = op.hx(s, p, ps);
         const V vs = vadd(h, cscale(c0r, c0i, ps));
         v[s] = vs;
-        if constexpr (std::is_same<V, float2>::value) bil_acc_df(ps, vs, df);
-        else bil_acc(ps, vs, acc[0], acc[1]);
+        if (pt) {
+            if constexpr (std::is_same<V, float2>::value) her_acc_df(pt[s], vs, df);
+            else her_acc(pt[s], vs, acc[0], acc[1]);
+        } else {
+            if constexpr (std::is_same<V, float2>::value) bil_acc_df(ps, vs, df);
+            else bil_acc(ps, vs, acc[0], acc[1]);
+        }
     }
     if constexpr (std::is_same<V, float2>::value) {
         acc[0] = df_value(df.rh, df.rl);
         acc[1] = df_value(df.ih, df.il);
     }
     store_partials<2>(acc, sm, part);
+}
+
+// Dual-space product v~ = (A + c0*) p~ = (A + c0)^dagger p~ for Hermitian A (App. A).
+template <class View, typename V>
+__global__ void __launch_bounds__(256) k_dual_mvm(View op, const V* __restrict__ pt, V* __restrict__ vt, int64_t n,
+                                                  double c0r, double c0i, const SeedState* __restrict__ st) {
+    if (st->done) return;
+    for (int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < n; s += int64_t(gridDim.x) * blockDim.x) {
+        const V ps = pt[s];
+        vt[s] = vadd(op.hx(s, pt, ps), cscale(c0r, -c0i, ps));
+    }
 }
 
 // alpha, and every active shift's zeta / gamma / c for block position j.
@@ -168,9 +186,11 @@ __global__ void __launch_bounds__(kScalarThreads) k_scalar_a(SeedState* st, cons
 }
 
 // r_{m+1} = r_m - alpha v (into the next ring slot); partials (r,r), ||r||^2.
+// Dual form (rt != null): also r~ <- r~ - conj(alpha) v~, and rho = <r~|r> (Hermitian).
 template <typename V>
 __global__ void __launch_bounds__(256) k_seed_update(V* ring, const V* __restrict__ v, int64_t n, int nslot,
-                                                     const SeedState* __restrict__ st, double* part) {
+                                                     const SeedState* __restrict__ st, double* part,
+                                                     V* __restrict__ rt, const V* __restrict__ vt) {
     if (st->done) return;
     __shared__ double sm[3 * 32];
     const int cur = st->slot, nxt = (cur + 1) % nslot;
@@ -183,6 +203,18 @@ __global__ void __launch_bounds__(256) k_seed_update(V* ring, const V* __restric
          s += int64_t(gridDim.x) * blockDim.x) {
         const V x = vsub(r[s], cscale(a.x, a.y, v[s]));
         rn[s] = x;
+        if (rt) {
+            const V y = vsub(rt[s], cscale(a.x, -a.y, vt[s]));
+            rt[s] = y;
+            if constexpr (std::is_same<V, float2>::value) {
+                her_acc_df(y, x, df);
+                norm_acc_df(x, df);
+            } else {
+                her_acc(y, x, acc[0], acc[1]);
+                acc[2] += norm2(x);
+            }
+            continue;
+        }
         if constexpr (std::is_same<V, float2>::value) {
             bil_acc_df(x, x, df);
             norm_acc_df(x, df);
@@ -280,17 +312,21 @@ __global__ void __launch_bounds__(kScalarThreads) k_scalar_b(SeedState* st, cons
 }
 
 // p = 2^f (r_{m+1} + beta p), r_{m+1} <- 2^f r_{m+1} (exact power-of-two rescale)
+// Dual form (rt != null): also p~ = 2^f (r~ + conj(beta) p~), r~ <- 2^f r~.
 template <typename V>
 __global__ void __launch_bounds__(256) k_update_p(V* ring, V* __restrict__ p, int64_t n,
-                                                  const SeedState* __restrict__ st) {
+                                                  const SeedState* __restrict__ st, V* __restrict__ rt,
+                                                  V* __restrict__ pt) {
     if (st->done) return;
     V* __restrict__ r = ring + int64_t(st->slot) * n;
     const double2 b = st->beta;
     const int f = st->fexp;
     if (f == 0) {
         for (int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < n;
-             s += int64_t(gridDim.x) * blockDim.x)
+             s += int64_t(gridDim.x) * blockDim.x) {
             p[s] = vadd(r[s], cscale(b.x, b.y, p[s]));
+            if (rt) pt[s] = vadd(rt[s], cscale(b.x, -b.y, pt[s]));
+        }
     } else {
         const double sc = ldexp(1.0, f);
         for (int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < n;
@@ -298,6 +334,11 @@ __global__ void __launch_bounds__(256) k_update_p(V* ring, V* __restrict__ p, in
             const V rs = r[s];
             p[s] = cscale(sc, 0.0, vadd(rs, cscale(b.x, b.y, p[s])));
             r[s] = cscale(sc, 0.0, rs);
+            if (rt) {
+                const V ts = rt[s];
+                pt[s] = cscale(sc, 0.0, vadd(ts, cscale(b.x, -b.y, pt[s])));
+                rt[s] = cscale(sc, 0.0, ts);
+            }
         }
     }
 }
@@ -389,9 +430,11 @@ __global__ void __launch_bounds__(256) k_flush(const V* __restrict__ ring, int n
 // ---------------------------------------------------------------------------
 // Initialisation: rho = (b,b), ||b||, r_0 = b in ring slot 0, p = b.
 // ---------------------------------------------------------------------------
+// Dual form (rt != null): r~_0 = p~_0 = b, rho = <b|b>.
 template <typename V>
 __global__ void __launch_bounds__(256) k_init_vectors(const V* __restrict__ b, V* __restrict__ ring,
-                                                      V* __restrict__ p, int64_t n, double* part) {
+                                                      V* __restrict__ p, int64_t n, double* part,
+                                                      V* __restrict__ rt, V* __restrict__ pt) {
     __shared__ double sm[3 * 32];
     double acc[3] = {0.0, 0.0, 0.0};
     DF4 df;
@@ -400,6 +443,18 @@ __global__ void __launch_bounds__(256) k_init_vectors(const V* __restrict__ b, V
         const V x = b[s];
         ring[s] = x;
         p[s] = x;
+        if (rt) {
+            rt[s] = x;
+            pt[s] = x;
+            if constexpr (std::is_same<V, float2>::value) {
+                her_acc_df(x, x, df);
+                norm_acc_df(x, df);
+            } else {
+                her_acc(x, x, acc[0], acc[1]);
+                acc[2] += norm2(x);
+            }
+            continue;
+        }
         if constexpr (std::is_same<V, float2>::value) {
             bil_acc_df(x, x, df);
             norm_acc_df(x, df);
@@ -476,6 +531,7 @@ struct SolverImpl {
     cudaStream_t st;
     int nslot, B, grid_vec, grid_flush;
     DevBuf<V> ring, p, v, Pbuf;
+    DevBuf<V> rt, pt, vt;     // dual-space vectors (App. A), allocated only for the dual form
     DevBuf<double> part;
     DevBuf<SeedState> state;
     DevBuf<double2> zeta, zeta_prev, shift, coef64;
@@ -498,15 +554,19 @@ struct SolverImpl {
         const double nb = double(n) * csz;
         {
             ProfScope ps("seed_mvm", st, 2 * nb + op->matrix_bytes(csz), op->hx_flops() + 16.0 * n);
-            k_mvm_dot<View, V><<<grid_vec, 256, 0, st>>>(view, p.p, v.p, n, pr.c0.x, pr.c0.y, state.p, part.p);
+            k_mvm_dot<View, V><<<grid_vec, 256, 0, st>>>(view, p.p, v.p, n, pr.c0.x, pr.c0.y, state.p, part.p, pt.p);
         }
         {
             ProfScope ps("shift_scalars", st, 0, 0);
             k_scalar_a<C><<<1, kScalarThreads, 0, st>>>(state.p, part.p, grid_vec, sh, pr.ns, B);
         }
+        if (pr.dual) {
+            ProfScope ps("seed_mvm", st, 2 * nb + op->matrix_bytes(csz), op->hx_flops() + 8.0 * n);
+            k_dual_mvm<View, V><<<grid_vec, 256, 0, st>>>(view, pt.p, vt.p, n, pr.c0.x, pr.c0.y, state.p);
+        }
         {
-            ProfScope ps("seed_update", st, 3 * nb, 20.0 * n);
-            k_seed_update<V><<<grid_vec, 256, 0, st>>>(ring.p, v.p, n, nslot, state.p, part.p);
+            ProfScope ps("seed_update", st, (pr.dual ? 6 : 3) * nb, 20.0 * n);
+            k_seed_update<V><<<grid_vec, 256, 0, st>>>(ring.p, v.p, n, nslot, state.p, part.p, rt.p, vt.p);
         }
         {
             ProfScope ps("shift_scalars", st, 0, 0);
@@ -514,7 +574,7 @@ struct SolverImpl {
         }
         {
             ProfScope ps("seed_p", st, 3 * nb, 8.0 * n);
-            k_update_p<V><<<grid_vec, 256, 0, st>>>(ring.p, p.p, n, state.p);
+            k_update_p<V><<<grid_vec, 256, 0, st>>>(ring.p, p.p, n, state.p, rt.p, pt.p);
         }
     }
 
@@ -554,6 +614,7 @@ struct SolverImpl {
         ring.alloc(size_t(nslot) * n);
         p.alloc(n);
         v.alloc(n);
+        if (pr.dual) { rt.alloc(n); pt.alloc(n); vt.alloc(n); }
         Pbuf.alloc(size_t(ns) * pr.n_out);
         part.alloc(size_t(grid_vec) * 4);
         state.alloc(1);
@@ -570,7 +631,7 @@ struct SolverImpl {
 
         {
             ProfScope ps("seed_init", st, 3.0 * n * csz, 12.0 * n);
-            k_init_vectors<V><<<grid_vec, 256, 0, st>>>((const V*)pr.b, ring.p, p.p, n, part.p);
+            k_init_vectors<V><<<grid_vec, 256, 0, st>>>((const V*)pr.b, ring.p, p.p, n, part.p, rt.p, pt.p);
         }
         {
             ProfScope ps("shift_scalars", st, 0, 0);
@@ -579,7 +640,7 @@ struct SolverImpl {
         }
         launches += 2;
         MSB_LAUNCH_CHECK();
-        const int64_t per_block = 2 + 5 * int64_t(B);   // kernels per block of iterations
+        const int64_t per_block = 2 + (pr.dual ? 6 : 5) * int64_t(B);   // kernels per block of iterations
         const int64_t max_blocks = (int64_t(pr.maxit) + B - 1) / B + 1;
         int64_t blocks = 0;
         if (prof_on()) {
@@ -672,6 +733,8 @@ struct SolverImpl {
 
 void multishift_solve(msb_op* op, const SolveProblem& pr, SolveResult& out, cudaStream_t st) {
     MSB_REQUIRE(pr.ns >= 1 && pr.ns <= kMaxShifts, "n_shifts must be in 1..4096");
+    MSB_REQUIRE(pr.dual || !op_has_flux(op),
+                "the operator is complex Hermitian (Peierls phases), not complex symmetric: use the dual solver");
     if (pr.prec == MSB_FP64) {
         SolverImpl<double2> s(pr, st);
         if (op->kind == 0) s.run(op, op->hub, out);
@@ -700,13 +763,12 @@ int pick_block(int block, msb_precision prec, int64_t n, int ns) {
 // ----------------------------------------------------------------------------
 // C ABI
 // ----------------------------------------------------------------------------
-extern "C" msb_status msb_multishift_bicg_solve(msb_op* A, msb_complex c0, const void* b,
-                                                const msb_complex* shifts, int n_shifts, double tol,
-                                                int maxit, int block, msb_precision prec, void* x,
-                                                int* iters, double* resid, int* converged,
-                                                msb_solve_info* info, void* stream) {
+static msb_status solve_entry(const char* fname, bool dual, msb_op* A, msb_complex c0, const void* b,
+                              const msb_complex* shifts, int n_shifts, double tol, int maxit, int block,
+                              msb_precision prec, void* x, int* iters, double* resid, int* converged,
+                              msb_solve_info* info, void* stream) {
     msb_status result = MSB_OK;
-    msb_status g = msb::guard("msb_multishift_bicg_solve", [&] {
+    msb_status g = msb::guard(fname, [&] {
         msb::require_device();
         MSB_REQUIRE(A != nullptr && b != nullptr && x != nullptr && shifts != nullptr, "NULL argument");
         MSB_REQUIRE(prec == MSB_FP64 || prec == MSB_FP32_MIXED, "unknown precision");
@@ -725,6 +787,7 @@ extern "C" msb_status msb_multishift_bicg_solve(msb_op* A, msb_complex c0, const
         pr.maxit = maxit;
         pr.block = msb::pick_block(block, prec, A->dim, n_shifts);
         pr.prec = prec;
+        pr.dual = dual;
         pr.shifts.resize(n_shifts);
         for (int k = 0; k < n_shifts; ++k) pr.shifts[k] = make_double2(shifts[k].re, shifts[k].im);
         msb::SolveResult out;
@@ -738,7 +801,7 @@ extern "C" msb_status msb_multishift_bicg_solve(msb_op* A, msb_complex c0, const
             *info = msb_solve_info{};
             info->iterations = out.iterations;
             info->n_converged = out.n_converged;
-            info->matvecs = out.iterations;
+            info->matvecs = (dual ? 2 : 1) * int64_t(out.iterations);
             info->flushes = out.flushes;
             info->seed_residual = out.seed_residual;
             double mx = 0;
@@ -750,8 +813,26 @@ extern "C" msb_status msb_multishift_bicg_solve(msb_op* A, msb_complex c0, const
             info->kernel_launches = out.launches;
         }
         result = out.status;
-        if (result != MSB_OK) msb::set_error_message("msb_multishift_bicg_solve: recurrence ended with status " +
-                                                     std::to_string(int(result)));
+        if (result != MSB_OK)
+            msb::set_error_message(std::string(fname) + ": recurrence ended with status " + std::to_string(int(result)));
     });
     return g != MSB_OK ? g : result;
+}
+
+extern "C" msb_status msb_multishift_bicg_solve(msb_op* A, msb_complex c0, const void* b,
+                                                const msb_complex* shifts, int n_shifts, double tol,
+                                                int maxit, int block, msb_precision prec, void* x,
+                                                int* iters, double* resid, int* converged,
+                                                msb_solve_info* info, void* stream) {
+    return solve_entry("msb_multishift_bicg_solve", false, A, c0, b, shifts, n_shifts, tol, maxit, block, prec, x,
+                       iters, resid, converged, info, stream);
+}
+
+extern "C" msb_status msb_multishift_bicg_dual_solve(msb_op* A, msb_complex c0, const void* b,
+                                                     const msb_complex* shifts, int n_shifts, double tol,
+                                                     int maxit, int block, msb_precision prec, void* x,
+                                                     int* iters, double* resid, int* converged,
+                                                     msb_solve_info* info, void* stream) {
+    return solve_entry("msb_multishift_bicg_dual_solve", true, A, c0, b, shifts, n_shifts, tol, maxit, block, prec, x,
+                       iters, resid, converged, info, stream);
 }

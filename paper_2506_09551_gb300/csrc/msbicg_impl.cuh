@@ -43,6 +43,7 @@ struct SolveProblem {
     int maxit = 1000;
     int block = 4;
     msb_precision prec = MSB_FP64;
+    bool dual = false;        // dual-space BiCG (App. A): A + c0 with A Hermitian, not complex symmetric
 };
 
 struct SolveResult {

@@ -33,8 +33,14 @@ static void build_hubbard(msb_op* op, const msb_model& m, int intermediate) {
     std::vector<int32_t> tu, td;
     std::vector<uint8_t> cu, cd;
     int Wu = 0, Wd = 0;
-    hop_table(m.L, op->sec_up, m.periodic != 0, op->host_up, tu, cu, Wu, m.lx);
-    hop_table(m.L, op->sec_dn, m.periodic != 0, op->host_dn, td, cd, Wd, m.lx);
+    std::vector<uint8_t> du, dd;
+    const bool flux = m.flux != 0.0;
+    hop_table(m.L, op->sec_up, m.periodic != 0, op->host_up, tu, cu, Wu, m.lx, flux ? &du : nullptr);
+    hop_table(m.L, op->sec_dn, m.periodic != 0, op->host_dn, td, cd, Wd, m.lx, flux ? &dd : nullptr);
+    if (flux) {
+        op->dirup.alloc(du.size()); op->dirup.upload(du.data(), du.size());
+        op->dirdn.alloc(dd.size()); op->dirdn.upload(dd.data(), dd.size());
+    }
     if (m.lx > 0 && m.tp != 0.0) {
         const auto bonds = lattice_bonds(m.L, true, m.lx, true);
         std::vector<int32_t> tu2, td2;
@@ -123,6 +129,10 @@ static void build_hubbard(msb_op* op, const msb_model& m, int intermediate) {
     h.hup2 = op->hup2.p; h.hdn2 = op->hdn2.p;
     h.nup2 = op->nup2.p; h.ndn2 = op->ndn2.p;
     h.t2 = m.tp;
+    h.dirup = op->dirup.p;
+    h.dirdn = op->dirdn.p;
+    h.cth = std::cos(m.flux / m.L);
+    h.sth = std::sin(m.flux / m.L);
     h.tf = float(m.t); h.Uf = float(m.U); h.Ucf = float(m.Uc);
     h.core = intermediate == 1 ? m.core_site : -1;
     h.L = m.L;

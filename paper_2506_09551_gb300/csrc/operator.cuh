@@ -83,6 +83,11 @@ struct HubView {
     const uint8_t* nup2;
     const uint8_t* ndn2;
     double t2;
+    // Peierls phases (flux through the ring): per hop entry 1 if the hop carries
+    // exp(+i theta), 0 for exp(-i theta); null without a flux
+    const uint8_t* dirup;
+    const uint8_t* dirdn;
+    double cth, sth;       // cos theta, sin theta, theta = flux / L
     double t, U, Uc;
     int core;              // core-hole site, -1: none (plain H)
     int L;                 // sites
@@ -98,9 +103,38 @@ struct HubView {
         return v;
     }
 
+    // Hopping sum with the Peierls phase of every hop (complex vectors only).
+    template <typename V>
+    __device__ __forceinline__ V hop_sum_phased(int64_t iu, int64_t id, const V* __restrict__ x) const {
+        using S = scalar_t<V>;
+        S ar = 0, ai = 0;
+        const S c = S(cth), s = S(sth);
+        const int nu = __ldg(nup + iu);
+        for (int e = 0; e < nu; ++e) {
+            const int32_t h = __ldg(hup + int64_t(e) * Dup + iu);
+            const V v = x[int64_t(h >> 1) * Ddn + id];
+            const S sg = (h & 1) ? S(-1) : S(1), ss = __ldg(dirup + int64_t(e) * Dup + iu) ? s : -s;
+            ar += sg * (c * v.x - ss * v.y);
+            ai += sg * (c * v.y + ss * v.x);
+        }
+        const int nd = __ldg(ndn + id);
+        const V* __restrict__ xrow = x + iu * Ddn;
+        for (int e = 0; e < nd; ++e) {
+            const int32_t h = __ldg(hdn + int64_t(e) * Ddn + id);
+            const V v = xrow[h >> 1];
+            const S sg = (h & 1) ? S(-1) : S(1), ss = __ldg(dirdn + int64_t(e) * Ddn + id) ? s : -s;
+            ar += sg * (c * v.x - ss * v.y);
+            ai += sg * (c * v.y + ss * v.x);
+        }
+        return mk(ar, ai);
+    }
+
     template <typename V>
     __device__ __forceinline__ V hx_at(int64_t iu, int64_t id, const V* __restrict__ x, V xs) const {
         using S = scalar_t<V>;
+        if constexpr (is_cplx_v<V>) {
+            if (dirup) return vaxpy(S(-t), hop_sum_phased(iu, id, x), vscale(diag<S>(iu, id), xs));
+        }
         V acc = vzero(xs);
         const int nu = __ldg(nup + iu);
         for (int e = 0; e < nu; ++e) {
@@ -220,6 +254,7 @@ struct msb_op {
     int intermediate = 0;
     int sec_up = 0, sec_dn = 0;  // electrons of this operator's sector
     msb::DevBuf<int32_t> hup, hdn, hup2, hdn2;
+    msb::DevBuf<uint8_t> dirup, dirdn;
     msb::DevBuf<uint8_t> nup, ndn, nup2, ndn2;
     msb::DevBuf<uint16_t> hdn16, hdn16p, slot16, dpos;
     msb::DevBuf<uint8_t> ndnp;
@@ -278,12 +313,22 @@ struct Bond { int i, j, cls; };
 std::vector<Bond> lattice_bonds(int L, bool periodic, int lx, bool diag);
 // ELL hop table [W][D] of the class-cls bonds, entries (target << 1) | neg, -1
 // empty; counts per state.
+// dir (optional): per entry 1 if <state|H|target> moves the electron along the
+// bond's direction (i -> j), for the Peierls phase of a flux.
 void hop_table_bonds(const std::vector<Bond>& bonds, int cls, int L, int n, const std::vector<uint32_t>& states,
-                     std::vector<int32_t>& table, std::vector<uint8_t>& count, int& W);
+                     std::vector<int32_t>& table, std::vector<uint8_t>& count, int& W,
+                     std::vector<uint8_t>* dir = nullptr);
 // The nearest-neighbour table of the chain or 2D cluster.
 void hop_table(int L, int n, bool periodic, const std::vector<uint32_t>& states,
-               std::vector<int32_t>& table, std::vector<uint8_t>& count, int& W, int lx = 0);
+               std::vector<int32_t>& table, std::vector<uint8_t>& count, int& W, int lx = 0,
+               std::vector<uint8_t>* dir = nullptr);
 void validate_model(const msb_model& m);
+// True for an operator with Peierls phases (complex Hermitian, not complex symmetric).
+inline bool op_has_flux(const msb_op* op) {
+    if (op->kind == 0) return op->hub.dirup != nullptr;
+    if (op->kind == 2) for (const msb_op* q : op->parts) if (q->hub.dirup != nullptr) return true;
+    return false;
+}
 // Electron counts of a model's sector: 0 ground, 1 intermediate, 2 final (operator.cu).
 void model_sector(const msb_model& m, int which, int& n_up, int& n_dn);
 // y = (A + c0) x for nvec columns (operator.cu).

@@ -302,6 +302,7 @@ void rixs_map_core(msb_op* opH_, msb_op* opHp_, const msb_model& m, const msb_ma
                    double E_G_in, const double* w_in, int n_in, const double* w, int n_w, double* I_out, bool I_dev,
                    msb_solve_info& info, cudaStream_t st, int64_t launches_so_far) {
     validate_model(m);
+    MSB_REQUIRE(m.flux == 0.0, "the map needs a real H (no flux): the dual solver takes complex H");
     MSB_REQUIRE(n_in >= 1 && n_in <= kMaxShifts, "n_in must be in 1..4096");
     MSB_REQUIRE(n_w >= 1, "n_w must be >= 1");
     MSB_REQUIRE(w_in && w && I_out, "NULL argument");
@@ -551,6 +552,7 @@ static void rixs_map_sites_impl(const msb_model& m, const msb_map_params& prm, c
                                 int n_q = 0) {
     validate_model(m);
     MSB_REQUIRE(m.o2_spin == 0 && m.o1_spin == 0, "the site batch supports the up-spin channel");
+    MSB_REQUIRE(m.flux == 0.0, "the map needs a real H (no flux)");
     MSB_REQUIRE(sites != nullptr && n_sites >= 1, "need at least one site");
     MSB_REQUIRE(n_in >= 1 && n_in <= kMaxShifts && int64_t(n_sites) * n_in <= 65535,
                 "n_sites * n_in must be at most 65535 (and n_in at most 4096)");
@@ -649,6 +651,7 @@ static void rixs_map_clusters_impl(const msb_model* models, int nc, const msb_ma
     for (int c = 0; c < nc; ++c) {
         validate_model(models[c]);
         MSB_REQUIRE(models[c].o2_spin == 0 && models[c].o1_spin == 0, "the cluster batch supports the up-spin channel");
+        MSB_REQUIRE(models[c].flux == 0.0, "the map needs a real H (no flux)");
         MSB_REQUIRE(models[c].n_up + 1 <= models[c].L, "the intermediate sector needs n_up + 1 <= L");
         MSB_REQUIRE(models[c].core_site >= 0 && models[c].core_site < models[c].L, "core_site out of range");
     }

@@ -25,7 +25,8 @@ class msb_complex(C.Structure):
 class msb_model(C.Structure):
     _fields_ = [("L", C.c_int), ("n_up", C.c_int), ("n_dn", C.c_int), ("periodic", C.c_int),
                 ("t", C.c_double), ("U", C.c_double), ("Uc", C.c_double), ("core_site", C.c_int),
-                ("o2_spin", C.c_int), ("o1_spin", C.c_int), ("lx", C.c_int), ("tp", C.c_double)]
+                ("o2_spin", C.c_int), ("o1_spin", C.c_int), ("lx", C.c_int), ("tp", C.c_double),
+                ("flux", C.c_double)]
 
 
 class msb_map_params(C.Structure):
@@ -81,6 +82,8 @@ SIGNATURES = {
     "msb_ground_state_noalloc": (_I, [_P, _D, _I, _P, _PD, _P, _PD, _P]),
     "msb_multishift_bicg_solve": (_I, [_P, msb_complex, _P, C.POINTER(msb_complex), _I, _D, _I, _I, _I, _P,
                                        _PI, _PD, _PI, C.POINTER(msb_solve_info), _P]),
+    "msb_multishift_bicg_dual_solve": (_I, [_P, msb_complex, _P, C.POINTER(msb_complex), _I, _D, _I, _I, _I, _P,
+                                            _PI, _PD, _PI, C.POINTER(msb_solve_info), _P]),
     "msb_bicgstab_solve": (_I, [_P, msb_complex, _P, C.POINTER(msb_complex), _I, _D, _I, _I, _P, _PI, _PD, _PI,
                                 C.POINTER(msb_solve_info), _P]),
     "msb_autotune": (_I, [C.POINTER(msb_model), _I, _I, _PI, _PI, _PD, _PD, _P]),

@@ -118,3 +118,25 @@ def test_kronecker_form_equals_generic_construction(L, nu, nd, core, periodic):
     B = hubbard.hamiltonian_kron(sec, 1.0, 8.0, 4.0, core, periodic)
     assert A.shape == B.shape and A.nnz == B.nnz
     assert abs(A - B).max() == 0.0
+
+
+@pytest.mark.parametrize("L,nu,nd,flux", [(5, 2, 2, 0.7), (6, 3, 2, 2.1), (4, 1, 2, -1.3)])
+def test_flux_hamiltonian_is_hermitian_with_twisted_u0_spectrum(L, nu, nd, flux):
+    """Peierls phases (a flux through the ring): H is complex Hermitian, and at U = 0 its
+    levels are sums of the twisted single-particle energies -2t cos(2 pi m / L + flux / L)."""
+    sec = hubbard.Sector(L, nu, nd)
+    H = hubbard.hamiltonian(sec, 1.0, 0.0, flux=flux).toarray()
+    assert np.iscomplexobj(H) and np.abs(H.imag).max() > 0
+    assert np.allclose(H, H.conj().T, atol=1e-14)
+    eps = -2.0 * np.cos(2 * np.pi * np.arange(L) / L + flux / L)
+    up = [sum(eps[list(c)]) for c in combinations(range(L), nu)]
+    dn = [sum(eps[list(c)]) for c in combinations(range(L), nd)]
+    assert np.allclose(np.linalg.eigvalsh(H), np.sort(np.add.outer(up, dn).ravel()), atol=1e-11)
+
+
+def test_flux_on_an_open_chain_is_a_gauge():
+    """On an open chain the phases can be gauged away: the spectrum does not depend on them."""
+    sec = hubbard.Sector(5, 2, 2)
+    H0 = hubbard.hamiltonian(sec, 1.0, 8.0, periodic=False).toarray()
+    H1 = hubbard.hamiltonian(sec, 1.0, 8.0, periodic=False, flux=1.9).toarray()
+    assert np.allclose(np.linalg.eigvalsh(H0), np.linalg.eigvalsh(H1), atol=1e-12)
