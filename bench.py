@@ -34,6 +34,7 @@ import argparse
 import math
 import json
 import os
+import shutil
 import statistics
 import subprocess
 import sys
@@ -269,7 +270,18 @@ def cpu_sampled_map(name: str, wl) -> dict:
         return {"value": None, "unit": "map points/s", "cores": host_cores(), "kind": "oracle",
                 "sample": "not sampled: no recorded per-row oracle counts"}
     P = host_cores()
-    base = "/dev/shm" if os.path.isdir("/dev/shm") else None
+    need = 2.2 * 16 * math.comb(wl.L, wl.n_up) * math.comb(wl.L, wl.n_dn) * 12     # both CSR matrices, with margin
+    base = None
+    for cand in ("/dev/shm", tempfile.gettempdir()):
+        try:
+            if os.path.isdir(cand) and shutil.disk_usage(cand).free > need:
+                base = cand
+                break
+        except OSError:
+            continue
+    if base is None:
+        return {"value": None, "unit": "map points/s", "cores": P, "kind": "oracle",
+                "sample": "not sampled: no scratch directory with room for the oracle's H and H'"}
     with tempfile.TemporaryDirectory(dir=base) as d:
         with _oracle_pool(1) as pool:
             t_build = pool.apply(_build_worker, ((d, wl.L, wl.n_up, wl.n_dn, wl.core_site),))
@@ -302,6 +314,14 @@ ORACLE_FULL_MAX_DIM = 20_000
 
 
 def run_cpu_baseline(name: str) -> dict:
+    try:
+        return _run_cpu_baseline(name)
+    except Exception as e:                       # the baseline never stops the GPU line
+        return {"value": None, "unit": "map points/s", "cores": host_cores(), "kind": "oracle",
+                "sample": f"failed: {type(e).__name__}: {e}"}
+
+
+def _run_cpu_baseline(name: str) -> dict:
     if name not in WORKLOADS:
         return {"value": None, "unit": "map points/s", "cores": host_cores(), "kind": "oracle",
                 "sample": f"not sampled for the batch workload {name}"}
@@ -789,7 +809,10 @@ def main():
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = run_cpu_baseline(args.workload)
             if args.workload == DEFAULT:
-                line["cpu_full_small_map"] = cpu_full_map(workloads.CHAIN8)
+                try:
+                    line["cpu_full_small_map"] = cpu_full_map(workloads.CHAIN8)
+                except Exception as e:
+                    line["cpu_full_small_map"] = {"value": None, "sample": f"failed: {type(e).__name__}: {e}"}
         elif not args.no_cpu_baseline:
             line["cpu_baseline"] = None
         print(json.dumps(line), flush=True)
