@@ -112,11 +112,11 @@ class Operator:
         self.dim = d.value
 
     @classmethod
-    def hubbard(cls, m: N.msb_model, sector=False) -> "Operator":
-        """H on the model's ground sector (sector 0 / False), H' on the intermediate sector
-        (1 / True) or H on the final sector of a spin-flip channel (2)."""
+    def hubbard(cls, m: N.msb_model, intermediate=False) -> "Operator":
+        """H on the model's ground sector (intermediate = 0 / False), H' on the intermediate
+        sector (1 / True) or H on the final sector of a spin-flip channel (2)."""
         h = C.c_void_p()
-        N.check(N.load().msb_op_create_hubbard(C.byref(m), int(sector), C.byref(h)))
+        N.check(N.load().msb_op_create_hubbard(C.byref(m), int(intermediate), C.byref(h)))
         return cls(h)
 
     @classmethod

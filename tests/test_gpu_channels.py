@@ -4,6 +4,7 @@ O1 = c_{j,up}, final states in another sector), the down-spin channel, and perio
 2D clusters with and without diagonal hopping t'."""
 import numpy as np
 import pytest
+import torch
 
 from oracle import rixs as orixs
 
@@ -29,11 +30,18 @@ def test_channel_and_cluster_maps(cuda, L, nu, nd, j, o2, o1, lx, tp):
     from paper_2506_09551_gb300 import api
     ref = _oracle(L, nu, nd, j, o2, o1, lx, tp)
     m = api.model(L, nu, nd, core_site=j, o2_spin=o2, o1_spin=o1, lx=lx, tp=tp)
-    I64, info64, st64 = api.rixs_map(m, api.map_params(solve_tol=1e-11, cf_tol=1e-10, precision=api.FP64), W_IN, W)
+    # the library's own ground state (its energy must agree) ...
+    _, info0, st0 = api.rixs_map(m, api.map_params(solve_tol=1e-10, cf_tol=1e-9, precision=api.FP64), W_IN, W)
+    assert st0 == 0 and abs(info0["E_G"] - ref.E_G) <= 1e-10 * abs(ref.E_G)
+    # ... and the maps from the oracle's |G> (open-shell fillings have a degenerate ground
+    # level, where each side may pick another vector of it)
+    G = torch.tensor(ref.G, dtype=torch.float64, device="cuda")
+    I64, info64, st64 = api.rixs_map(m, api.map_params(solve_tol=1e-11, cf_tol=1e-10, precision=api.FP64), W_IN, W,
+                                     G=G, E_G=ref.E_G)
     assert st64 == 0
-    assert abs(info64["E_G"] - ref.E_G) <= 1e-10 * abs(ref.E_G)
     e64 = orixs.relative_l2(I64, ref.I)
-    I32, _, st32 = api.rixs_map(m, api.map_params(solve_tol=1e-8, cf_tol=1e-5, precision=api.FP32_MIXED), W_IN, W)
+    I32, _, st32 = api.rixs_map(m, api.map_params(solve_tol=1e-8, cf_tol=1e-5, precision=api.FP32_MIXED), W_IN, W,
+                                G=G, E_G=ref.E_G)
     e32 = orixs.relative_l2(I32, ref.I)
     print(f"L={L} ({nu},{nd}) O2 spin {o2} O1 spin {o1} lx={lx} t'={tp}: FP64 {e64:.2e}, FP32-mixed {e32:.2e}")
     assert e64 <= 1e-8 and e32 <= 1e-4

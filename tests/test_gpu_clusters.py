@@ -50,7 +50,7 @@ def test_direct_sum_rejections(cuda):
     with pytest.raises(native.MsbError):
         api.Operator.direct_sum([a, csr])
     with pytest.raises(native.MsbError):
-        api.Operator.direct_sum([a] * 5)
+        api.Operator.direct_sum([a] * 17)
 
 
 def test_cluster_map_matches_separate_maps_and_oracle(cuda):
