@@ -9,24 +9,33 @@ energy, the sector maps and the batched continued fraction of the second step.
 
 Prints one JSON line (rank 0).  `value` times msb_rixs_map_ops (operators
 built beforehand, map left on the device) with CUDA events on the calling
-stream; `e2e` times msb_rixs_map (host grids in, host map out, operators
-built inside the call) with a wall clock.  Every kernel launch inside the
-timed steps is bracketed by CUDA events by the library's profiler, which
-gives the dominant kernel's achieved bandwidth / FLOP rate for `roofline`.
-Under torchrun each rank computes the map of its own core site (independent
-problems, no collective on the data path): weak scaling.
+stream, with the library profiler off (the solve replays its CUDA graphs).
+One more map with the profiler on (every launch bracketed by CUDA events on
+its stream) gives the kernel shares and the dominant kernel's roofline.
+`e2e` times msb_rixs_map (host grids in, host map out, operators built inside
+the call) with a wall clock.  For the default FP32-mixed L = 14 workload the
+line adds `precision_comparison`: the same map once in the plain FP64 form
+(speed-up and relative L2 difference).  Under torchrun each rank computes the
+map of its own core site (independent problems, no collective on the data
+path): weak scaling.
 
-Workloads (--workload): hubbard-L12-fp64 (default), hubbard-L8-fp64,
-hubbard-L14-mixed, hubbard-L14-fp64 (the same ring in FP64, for the precision
-comparison; use --n-in to shorten it), hubbard-L12x12rhs-mixed (one right-hand
-side per core site, one call), hubbard-L10-11-12-clusters-mixed (three clusters
-of uneven size in one solve and one continued fraction; its line adds
-`separate_maps`, the same clusters as separate calls), hubbard-L12-q12-mixed
-(momentum-resolved maps: the coherent sum over the 12 core sites at the 12
-momenta 2 pi k / 12), random-csr-fp64 and
-random-csr-mixed (n = 2^22, 256 shifts; one step = the multi-shift solve).
-`cpu_baseline` (the oracle on one host core, a bounded sample scaled to the
-whole map) is sampled for the single-map workloads up to L = 12.
+Workloads (--workload): hubbard-L14-mixed (default: L = 14, 201 x 400 points,
+FP32 vectors and apply, FP64 scalars), hubbard-L14-fp64, hubbard-L12-fp64,
+hubbard-L8-fp64, hubbard-L12x12rhs-mixed (one right-hand side per core site,
+one joint solve), hubbard-L10-11-12-clusters-mixed (three clusters of uneven
+size in one solve and one continued fraction; its line adds `separate_maps`),
+hubbard-L12-q12-mixed (momentum-resolved maps over the 12 core sites),
+random-csr-fp64 and random-csr-mixed (n = 2^22, 256 shifts; one step = the
+multi-shift solve), solve-sweep-L12 (Fig. 4: MSBiCG vs per-energy BiCGStab,
+MVMs, seconds and memory against the number of incident energies) and
+cf-tolerance-study (map error against the continued fraction's stopping rule).
+
+`cpu_baseline`: the oracle on the host cores (a process pool, the core count
+from the affinity mask): the whole map for small workloads, and for L = 12 / 14
+a bounded, labelled sample (the oracle's build of H and H' and its sparse
+products timed with every core busy) scaled with the oracle's own per-row
+counts.  The default line also carries the oracle's whole L = 8 map timed on
+all cores (`cpu_full_small_map`).
 """
 from __future__ import annotations
 
@@ -71,6 +80,8 @@ FP64_FORM = {"hubbard-L14-mixed": "hubbard-L14-fp64"}
 DEFAULT = "hubbard-L14-mixed"
 # the solve-cost sweep of Fig. 4 (MSBiCG vs per-energy BiCGStab on the GPU)
 SWEEP = "solve-sweep-L12"
+# the continued fraction's stopping rule against the map error
+CF_STUDY = "cf-tolerance-study"
 SWEEP_N_IN = (10, 30, 100, 300)
 # random complex-symmetric stress workload: name -> precision, tolerance
 CSR_WORKLOADS = {"random-csr-fp64": (0, 1e-10), "random-csr-mixed": (1, 1e-7)}
@@ -537,6 +548,51 @@ def gpu_arm_sweep(args, rank, world):
             "sweep": rows}
 
 
+def gpu_arm_cf_study(args, rank, world):
+    """The continued fraction's stopping rule against accuracy: maps of the L = 12
+    workload (all 101 x 400 points) and of 21 incident energies of the L = 14 workload at
+    several cf_tol, each against the same map with a converged fraction (FP64, cf_tol
+    1e-13 at L = 12, 1e-11 at L = 14): relative L2 error, largest row error, depth range
+    and seconds per map (wall clock, profiler off)."""
+    import torch
+    from paper_2506_09551_gb300 import api, native
+
+    native.load()
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+
+    def run(m, prec, stol, ctol, w_in, w):
+        p = api.map_params(Gamma=0.3, eta=0.1, solve_tol=stol, cf_tol=ctol, precision=prec, cf_maxdepth=8000)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        I, info, st = api.rixs_map(m, p, w_in, w)
+        torch.cuda.synchronize()
+        return I, {"seconds": time.perf_counter() - t0, "depth_min": info["cf_depth_min"],
+                   "depth_max": info["cf_depth_max"]}
+
+    def err(I, ref):
+        rows = np.linalg.norm(I - ref, axis=1) / np.linalg.norm(ref, axis=1)
+        return {"rel_l2": float(np.linalg.norm(I - ref) / np.linalg.norm(ref)), "row_max": float(rows.max())}
+
+    out = []
+    cases = [(workloads.CHAIN12, None, 1e-13, [(0, 1e-10, t) for t in (1e-11, 1e-10, 1e-9, 1e-8, 1e-7, 1e-6)] +
+              [(1, 1e-8, t) for t in (1e-8, 1e-7, 1e-6, 1e-5, 1e-4)]),
+             (workloads.CHAIN14, 10, 1e-11, [(1, 1e-8, t) for t in (1e-8, 1e-7, 1e-6, 1e-5, 1e-4)])]
+    for wl, stride, ref_tol, runs in cases:
+        m = api.model(wl.L, wl.n_up, wl.n_dn)
+        w_in = wl.w_in[::stride] if stride else wl.w_in
+        ref, r0 = run(m, 0, 1e-10, ref_tol, w_in, wl.w)
+        out.append({"workload": wl.name, "n_w_in": len(w_in), "precision": "FP64", "cf_tol": ref_tol,
+                    "reference": True, **r0})
+        for prec, stol, ctol in runs:
+            I, r = run(m, prec, stol, ctol, w_in, wl.w)
+            rec = {"workload": wl.name, "n_w_in": len(w_in), "precision": "FP64" if prec == 0 else "FP32-mixed",
+                   "solve_tol": stol, "cf_tol": ctol, **r, **err(I, ref)}
+            out.append(rec)
+            print(f"[bench] cf study {rec}", file=sys.stderr, flush=True)
+    return {"metric": "continued-fraction stopping rule vs map error", "n_gpus": 1,
+            "config": {"workload": args.workload}, "data": "synthetic", "study": out}
+
+
 def gpu_arm(args, rank, world):
     import torch
     from paper_2506_09551_gb300 import api, native
@@ -772,7 +828,7 @@ def main():
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + sorted(CSR_WORKLOADS) + sorted(CLUSTERS) + [SWEEP],
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + sorted(CSR_WORKLOADS) + sorted(CLUSTERS) + [SWEEP, CF_STUDY],
                     default=DEFAULT)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end map (profiling runs)")
@@ -792,9 +848,10 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         dist.init_process_group("nccl")
-    if args.workload == SWEEP:
+    if args.workload in (SWEEP, CF_STUDY):
         if rank == 0:
-            print(json.dumps(gpu_arm_sweep(args, rank, world)), flush=True)
+            fn = gpu_arm_sweep if args.workload == SWEEP else gpu_arm_cf_study
+            print(json.dumps(fn(args, rank, world)), flush=True)
         return
     if args.workload in CSR_WORKLOADS:
         line = gpu_arm_csr(args, rank, world)

@@ -395,8 +395,9 @@ msb_status msb_rixs_map(const msb_model *model, const msb_map_params *params,
 /* Timed trials, on the operators of `model`, of the launch choices that leave
  * the results unchanged up to the rounding order of a block reduction: the lag
  * B in {1, 2, 4, 8, 16} of the fused per-shift update of a solve with n_in
- * shifts (FP32 or FP64 per `prec`), and, for MSB_FP64, the threads per CTA
- * (128 or 256) of the row-tiled continued-fraction apply.  Each candidate is
+ * shifts (FP32 or FP64 per `prec`), and the shape of the row-tiled
+ * continued-fraction apply: threads per CTA (128 or 256) for MSB_FP64, columns
+ * per CTA (1 or 2) for MSB_FP32_MIXED (returned in *cf_threads).  Each candidate is
  * timed with CUDA events as the difference of a 2K- and a K-iteration run (the
  * allocations of a call cancel).  The fastest choices are cached for the whole
  * process, keyed by the problem's shape (intermediate dimension, n_in and
@@ -404,7 +405,7 @@ msb_status msb_rixs_map(const msb_model *model, const msb_map_params *params,
  * used by every later call that leaves them automatic (params->block or the
  * solver's `block` = 0).  HOST outputs (may be NULL): the choices, and the
  * measured milliseconds per iteration for each B (5 values) and per level for
- * each thread count (2 values, 0 for FP32).  Allocates and frees its own work
+ * each apply shape (2 values).  Allocates and frees its own work
  * vectors; synchronises `stream`.  The paper has no counterpart. */
 msb_status msb_autotune(const msb_model *model, msb_precision prec, int n_in, int *block, int *cf_threads,
                         double *block_ms, double *cf_ms, void *stream);

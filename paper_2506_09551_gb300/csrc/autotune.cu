@@ -136,13 +136,14 @@ static void autotune_impl(const msb_model& m, msb_precision prec, int n_in, Tune
             if (out.block_ms[i] < best) { best = out.block_ms[i]; out.block = Bs[i]; }
         }
     }
-    // 2. threads per CTA of the FP64 row-tiled continued-fraction apply
-    if (prec == MSB_FP64) {
+    // 2. the row-tiled continued-fraction apply: threads per CTA (FP64: 128 or 256) or
+    // columns per CTA (FP32: 1 or 2)
+    {
         DevBuf<C> phi(size_t(n_in) * D);
         k_tune_fill<C><<<grid_for(int64_t(n_in) * D, 256, 4), 256, 0, st>>>(phi.p, int64_t(n_in) * D, 0xCF11ull);
         std::vector<double> w(8), I(size_t(n_in) * 8);
         for (int i = 0; i < 8; ++i) w[i] = double(i);
-        const int Ts[2] = {128, 256};
+        const int Ts[2] = {prec == MSB_FP64 ? 128 : 1, prec == MSB_FP64 ? 256 : 2};
         double best = 1e300;
         for (int i = 0; i < 2; ++i) {
             g_cf_threads_force = Ts[i];

@@ -961,6 +961,171 @@ __global__ void __launch_bounds__(256, 6) k_cf_apply_hub_f2x2(HubView h0, const 
     if (threadIdx.x == 0) part[int64_t(blockIdx.y) * gridDim.x + blockIdx.x] = tot;
 }
 
+// The FP32 pass A for two columns per CTA (one operator for all columns): the two
+// columns' row u share the up-spin offsets, the down-spin table entries, the index
+// arithmetic, the occupation strings and the loop control, so the issue-bound
+// kernel spends about a third fewer instructions per column.  Both rows sit in
+// shared memory at the sector's bank-aware slots.  blockIdx.y indexes a pair of
+// active columns (cols[2y], cols[2y + 1]); a missing second column (odd count)
+// is skipped.  Partial products go to part[(2y + j) * gridDim.x + u], the layout
+// of the one-column kernel.
+template <bool Signed>
+__global__ void __launch_bounds__(256, 4) k_cf_apply_hub_f2x2c2(HubView h, const float2* __restrict__ Vk,
+                                                                const float2* __restrict__ Vkm1,
+                                                                float2* __restrict__ W, int64_t ld,
+                                                                const int* __restrict__ cols, int na, CFCoef cf,
+                                                                double* part) {
+    const int u = blockIdx.x;
+    const int j0 = 2 * blockIdx.y;
+    const bool two = j0 + 1 < na;
+    const int c0 = cols[j0];
+    const int c1 = two ? cols[j0 + 1] : c0;
+    const int L = h.L;
+    const int Ddn = int(h.Ddn);
+    const int half = Ddn >> 1;
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    float2* row0 = reinterpret_cast<float2*>(sm_raw);               // row u of column 0, then two zeros
+    float2* row1 = row0 + (Ddn + 2);                                // row u of column 1, then two zeros
+    float* lut0 = reinterpret_cast<float*>(row1 + (Ddn + 2));       // 3 (L + 1) diagonal values * sig, per column
+    float* lut1 = lut0 + 3 * (L + 1);
+    __shared__ int s_uoff[kMaxHops];
+    __shared__ float s_usg[kMaxHops];
+    __shared__ float red[64];
+    const float2* __restrict__ V0 = Vk + int64_t(c0) * ld;
+    const float2* __restrict__ V1 = Vk + int64_t(c1) * ld;
+    const float4* __restrict__ P04 = reinterpret_cast<const float4*>(Vkm1 + int64_t(c0) * ld);
+    const float4* __restrict__ P14 = reinterpret_cast<const float4*>(Vkm1 + int64_t(c1) * ld);
+    float4* __restrict__ W04 = reinterpret_cast<float4*>(W + int64_t(c0) * ld);
+    float4* __restrict__ W14 = reinterpret_cast<float4*>(W + int64_t(c1) * ld);
+    const int rbase = u * Ddn;
+    const float sig0 = cf.sigf[c0], cB0 = cf.cBf[c0], sig1 = cf.sigf[c1], cB1 = cf.cBf[c1];
+    const uint32_t su = __ldg(h.sup + u);
+    const int nu = __ldg(h.nup + u);
+    const uint32_t* sl2 = reinterpret_cast<const uint32_t*>(h.slot16);   // slots of positions 2i, 2i + 1
+    {
+        const float4* src0 = reinterpret_cast<const float4*>(V0 + rbase);
+        const float4* src1 = reinterpret_cast<const float4*>(V1 + rbase);
+        for (int i = threadIdx.x; i < half; i += blockDim.x) {
+            const uint32_t sp = __ldg(sl2 + i);
+            const float4 a = src0[i], b = src1[i];
+            row0[sp & 0xFFFFu] = make_float2(a.x, a.y);
+            row0[sp >> 16] = make_float2(a.z, a.w);
+            row1[sp & 0xFFFFu] = make_float2(b.x, b.y);
+            row1[sp >> 16] = make_float2(b.z, b.w);
+        }
+        if (threadIdx.x == 0) {
+            reinterpret_cast<float4*>(row0)[half] = make_float4(0.f, 0.f, 0.f, 0.f);
+            reinterpret_cast<float4*>(row1)[half] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    }
+    for (int i = threadIdx.x; i < 3 * (L + 1); i += blockDim.x) {
+        const int p = i % (L + 1), nb = i / (L + 1);
+        const float e = h.Uf * float(p) - h.Ucf * float(nb);
+        lut0[i] = sig0 * e;
+        lut1[i] = sig1 * e;
+    }
+    if (threadIdx.x < nu) {
+        const int32_t ent = __ldg(h.hup + int64_t(threadIdx.x) * h.Dup + u);
+        s_uoff[threadIdx.x] = ((ent >> 1) * Ddn) >> 1;           // in float4 units
+        s_usg[threadIdx.x] = (Signed && (ent & 1)) ? -1.f : 1.f;
+    }
+    __syncthreads();
+    const int core = h.core;
+    const int ubits = core >= 0 ? int((su >> core) & 1u) : 0;
+    const float mt0 = -h.tf * sig0, mt1 = -h.tf * sig1;
+    const float4* __restrict__ V04 = reinterpret_cast<const float4*>(V0);
+    const float4* __restrict__ V14 = reinterpret_cast<const float4*>(V1);
+    const uint32_t* __restrict__ t32 = reinterpret_cast<const uint32_t*>(h.hdn16p);
+    const uint16_t* __restrict__ n16 = reinterpret_cast<const uint16_t*>(h.ndnp);
+    const uint2* __restrict__ sd2 = reinterpret_cast<const uint2*>(h.sdnp);
+    float dh0 = 0.f, dl0 = 0.f, dh1 = 0.f, dl1 = 0.f;
+    const int iters = (half + blockDim.x - 1) / blockDim.x;
+    const int step = Ddn >> 1;
+    for (int it = 0; it < iters; ++it) {
+        const int q0 = it * blockDim.x + threadIdx.x;
+        const bool act = q0 < half;
+        const int q = act ? q0 : 0;
+        float4 A = make_float4(0.f, 0.f, 0.f, 0.f), B = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int e = 0; e < nu; ++e) {
+            const int o = s_uoff[e] + q;
+            const float4 v = V04[o], w4 = V14[o];
+            if constexpr (Signed) {
+                const float g = s_usg[e];
+                A.x = fmaf(g, v.x, A.x); A.y = fmaf(g, v.y, A.y); A.z = fmaf(g, v.z, A.z); A.w = fmaf(g, v.w, A.w);
+                B.x = fmaf(g, w4.x, B.x); B.y = fmaf(g, w4.y, B.y); B.z = fmaf(g, w4.z, B.z); B.w = fmaf(g, w4.w, B.w);
+            } else {
+                A.x += v.x; A.y += v.y; A.z += v.z; A.w += v.w;
+                B.x += w4.x; B.y += w4.y; B.z += w4.z; B.w += w4.w;
+            }
+        }
+        const uint32_t nn = __ldg(n16 + q);
+        const int ndw = __reduce_max_sync(0xffffffffu, act ? max(int(nn & 0xFFu), int(nn >> 8)) : 0);
+        const uint32_t* __restrict__ tp = t32 + q;
+        for (int k = 0; k < ndw; ++k, tp += step) {
+            const uint32_t ta = __ldg(tp);
+            const int ia = int((ta & 0xFFFFu) >> 1), ib = int(ta >> 17);
+            const float2 va = row0[ia], vb = row0[ib], wa = row1[ia], wb = row1[ib];
+            if constexpr (Signed) {
+                const float ga = (ta & 1u) ? -1.f : 1.f, gb = (ta & 0x10000u) ? -1.f : 1.f;
+                A.x = fmaf(ga, va.x, A.x); A.y = fmaf(ga, va.y, A.y); A.z = fmaf(gb, vb.x, A.z); A.w = fmaf(gb, vb.y, A.w);
+                B.x = fmaf(ga, wa.x, B.x); B.y = fmaf(ga, wa.y, B.y); B.z = fmaf(gb, wb.x, B.z); B.w = fmaf(gb, wb.y, B.w);
+            } else {
+                A.x += va.x; A.y += va.y; A.z += vb.x; A.w += vb.y;
+                B.x += wa.x; B.y += wa.y; B.z += wb.x; B.w += wb.y;
+            }
+        }
+        const uint2 sd = __ldg(sd2 + q);
+        const int nb0 = core >= 0 ? ubits + int((sd.x >> core) & 1u) : 0;
+        const int nb1 = core >= 0 ? ubits + int((sd.y >> core) & 1u) : 0;
+        const int l0 = __popc(su & sd.x) + nb0 * (L + 1), l1 = __popc(su & sd.y) + nb1 * (L + 1);
+        if (!act) continue;                                      // warp-uniform part done
+        const int g4 = (rbase >> 1) + q;
+        {
+            const float4 x = V04[g4];
+            const float d0 = lut0[l0], d1 = lut0[l1];
+            float4 wv;
+            wv.x = fmaf(mt0, A.x, d0 * x.x);
+            wv.y = fmaf(mt0, A.y, d0 * x.y);
+            wv.z = fmaf(mt0, A.z, d1 * x.z);
+            wv.w = fmaf(mt0, A.w, d1 * x.w);
+            if (cB0 != 0.f) {
+                const float4 y = __ldcs(P04 + g4);
+                wv.x = fmaf(-cB0, y.x, wv.x); wv.y = fmaf(-cB0, y.y, wv.y);
+                wv.z = fmaf(-cB0, y.z, wv.z); wv.w = fmaf(-cB0, y.w, wv.w);
+            }
+            __stcs(W04 + g4, wv);
+            df_add_prod(dh0, dl0, x.x, wv.x);
+            df_add_prod(dh0, dl0, x.y, wv.y);
+            df_add_prod(dh0, dl0, x.z, wv.z);
+            df_add_prod(dh0, dl0, x.w, wv.w);
+        }
+        if (two) {
+            const float4 x = V14[g4];
+            const float d0 = lut1[l0], d1 = lut1[l1];
+            float4 wv;
+            wv.x = fmaf(mt1, B.x, d0 * x.x);
+            wv.y = fmaf(mt1, B.y, d0 * x.y);
+            wv.z = fmaf(mt1, B.z, d1 * x.z);
+            wv.w = fmaf(mt1, B.w, d1 * x.w);
+            if (cB1 != 0.f) {
+                const float4 y = __ldcs(P14 + g4);
+                wv.x = fmaf(-cB1, y.x, wv.x); wv.y = fmaf(-cB1, y.y, wv.y);
+                wv.z = fmaf(-cB1, y.z, wv.z); wv.w = fmaf(-cB1, y.w, wv.w);
+            }
+            __stcs(W14 + g4, wv);
+            df_add_prod(dh1, dl1, x.x, wv.x);
+            df_add_prod(dh1, dl1, x.y, wv.y);
+            df_add_prod(dh1, dl1, x.z, wv.z);
+            df_add_prod(dh1, dl1, x.w, wv.w);
+        }
+    }
+    const double t0 = block_sum_df(dh0, dl0, red);
+    if (threadIdx.x == 0) part[int64_t(j0) * gridDim.x + u] = t0;
+    __syncthreads();
+    const double t1 = block_sum_df(dh1, dl1, red);
+    if (two && threadIdx.x == 0) part[int64_t(j0 + 1) * gridDim.x + u] = t1;
+}
+
 // Pass A for any operator view (CSR): flat grid over elements.
 template <class View, typename C>
 __global__ void __launch_bounds__(256) k_cf_apply_gen(View op, const C* __restrict__ Vk, const C* __restrict__ Vkm1,
@@ -1047,18 +1212,20 @@ __global__ void __launch_bounds__(256) k_cf_orth(const C* __restrict__ Vk, C* __
     float hi = 0.f, lo = 0.f;
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    // evict-first loads and stores: this pass streams whole columns that are not read
+    // again soon, and should not push out of L2 the column another group's apply gathers from
     for (; i + stride < nv; i += 2 * stride) {      // two independent loads in flight per stream
-        V16 x0 = w4[i], x1 = w4[i + stride];
-        const V16 a0 = v4[i], a1 = v4[i + stride];
+        V16 x0 = __ldcs(w4 + i), x1 = __ldcs(w4 + i + stride);
+        const V16 a0 = __ldcs(v4 + i), a1 = __ldcs(v4 + i + stride);
         orth_step(a0, x0, mc, acc, hi, lo);
         orth_step(a1, x1, mc, acc, hi, lo);
-        w4[i] = x0;
-        w4[i + stride] = x1;
+        __stcs(w4 + i, x0);
+        __stcs(w4 + i + stride, x1);
     }
     if (i < nv) {
-        V16 x0 = w4[i];
-        orth_step(v4[i], x0, mc, acc, hi, lo);
-        w4[i] = x0;
+        V16 x0 = __ldcs(w4 + i);
+        orth_step(__ldcs(v4 + i), x0, mc, acc, hi, lo);
+        __stcs(w4 + i, x0);
     }
     if constexpr (std::is_same<S, float>::value) {
         const double tot = block_sum_df(hi, lo, reinterpret_cast<float*>(sm));
@@ -1166,6 +1333,7 @@ static void cf_impl(const CFColumns& P, const View& view, const double* w, int n
     const int grid = grid_for(ld / per, 256, 4);
     int64_t hub_smem = 0;
     bool rows = false, pair = false, fx = false, sgn = false;
+    int cpc = 1;                               // columns per CTA of the FP32 row-tiled apply
     int fx_threads = 256;
     int nblkA = grid;
     std::vector<HubView> hviews;
@@ -1197,6 +1365,11 @@ static void cf_impl(const CFColumns& P, const View& view, const double* w, int n
             const int t = tuned_cf_threads(maxDdn, maxDup, MSB_FP64);
             if (t == 128 || t == 256) fx_threads = t;
         }
+        // FP32: two columns per CTA by default (the autotuner may choose one)
+        if (!multi && pair && hviews[0].slot16 != nullptr) {
+            const int t = tuned_cf_threads(maxDdn, maxDup, MSB_FP32_MIXED);
+            cpc = (t == 1) ? 1 : 2;
+        }
         fx = fx && rows;
         pair = pair && rows;
         if (rows) {
@@ -1205,7 +1378,15 @@ static void cf_impl(const CFColumns& P, const View& view, const double* w, int n
             if (fx)
                 fn = multi ? (sgn ? (const void*)k_cf_apply_hub_fx<true, true> : (const void*)k_cf_apply_hub_fx<true, false>)
                            : (sgn ? (const void*)k_cf_apply_hub_fx<false, true> : (const void*)k_cf_apply_hub_fx<false, false>);
-            else if (pair)
+            else if (pair && cpc == 2) {
+                fn = sgn ? (const void*)k_cf_apply_hub_f2x2c2<true> : (const void*)k_cf_apply_hub_f2x2c2<false>;
+                hub_smem = 2 * (maxDdn + 2) * int64_t(sizeof(C)) + 2 * 3 * (maxL + 1) * 4;
+                if (hub_smem > 200 * 1024) {               // rows too long for two per CTA
+                    cpc = 1;
+                    hub_smem = (maxDdn + 2) * int64_t(sizeof(C)) + 3 * (maxL + 1) * 8;
+                    fn = sgn ? (const void*)k_cf_apply_hub_f2x2<false, true> : (const void*)k_cf_apply_hub_f2x2<false, false>;
+                }
+            } else if (pair)
                 fn = multi ? (sgn ? (const void*)k_cf_apply_hub_f2x2<true, true> : (const void*)k_cf_apply_hub_f2x2<true, false>)
                            : (sgn ? (const void*)k_cf_apply_hub_f2x2<false, true> : (const void*)k_cf_apply_hub_f2x2<false, false>);
             else
@@ -1252,34 +1433,80 @@ static void cf_impl(const CFColumns& P, const View& view, const double* w, int n
     for (int c = 0; c < nv; ++c)
         if (hn0[c] > 0.0) hcols[nact++] = c;
     cols.upload(hcols.data(), std::max(nact, 1), st);
-    // algorithmic bytes / flops of the active columns (recounted when the set shrinks)
-    double act_elems = 0, apply_bytes = 0, apply_flops = 0;
-    auto recount = [&] {
-        act_elems = apply_bytes = apply_flops = 0;
-        for (int i = 0; i < nact; ++i) {
-            const int c = hcols[i];
-            const msb_op* o = P.ops[P.q[c]];
-            act_elems += double(nlen[c]);
-            apply_bytes += 3.0 * double(nlen[c]) * sizeof(C) + o->matrix_bytes(sizeof(C));
-            apply_flops += o->hx_flops() + 8.0 * double(nlen[c]);
+    const dim3 gridA(unsigned(nblkA), 1);
+    // Two column groups on two streams: the apply of one group (bound by issue and the
+    // L1/shared pipe) overlaps the orth pass of the other (bound by DRAM).  Each group's
+    // levels are ordered on its own stream; the groups meet at every convergence check.
+    // With the profiler on, one group, so that every launch is timed alone.
+    const int ngrp = prof_on() ? 1 : 2;
+    cudaStream_t gs[2] = {st, nullptr};
+    cudaEvent_t gev = nullptr;
+    if (ngrp == 2) {
+        MSB_CUDA(cudaStreamCreateWithFlags(&gs[1], cudaStreamNonBlocking));
+        MSB_CUDA(cudaEventCreateWithFlags(&gev, cudaEventDisableTiming));
+    }
+    struct StreamGuard {
+        cudaStream_t s; cudaEvent_t e;
+        ~StreamGuard() { if (s) { cudaStreamSynchronize(s); cudaStreamDestroy(s); } if (e) cudaEventDestroy(e); }
+    } sguard{gs[1], gev};
+    DevBuf<int> gcols_d[2];
+    DevBuf<double> gpart[2];
+    std::vector<int> gcols[2];
+    for (int g = 0; g < ngrp; ++g) {
+        gcols_d[g].alloc(std::max(nv, 1));
+        gpart[g].alloc(size_t(std::max(grid, nblkA)) * nv);
+    }
+    auto split = [&] {                              // active columns -> groups, interleaved
+        for (int g = 0; g < ngrp; ++g) gcols[g].clear();
+        for (int i = 0; i < nact; ++i) gcols[i % ngrp].push_back(hcols[i]);
+        for (int g = 0; g < ngrp; ++g)
+            if (!gcols[g].empty()) gcols_d[g].upload(gcols[g].data(), gcols[g].size(), st);
+        if (ngrp == 2) {                            // the lists are uploaded on st
+            MSB_CUDA(cudaEventRecord(gev, st));
+            MSB_CUDA(cudaStreamWaitEvent(gs[1], gev, 0));
         }
     };
-    recount();
-    const dim3 gridA(unsigned(nblkA), 1);
-    int k = 0;
-    while (nact > 0 && k < maxdepth) {
+    split();
+    double grp_bytes[2], grp_flops[2], grp_elems[2];
+    auto regroup_counts = [&] {
+        for (int g = 0; g < ngrp; ++g) {
+            grp_bytes[g] = grp_flops[g] = grp_elems[g] = 0;
+            for (int c : gcols[g]) {
+                const msb_op* o = P.ops[P.q[c]];
+                grp_elems[g] += double(nlen[c]);
+                grp_bytes[g] += 3.0 * double(nlen[c]) * sizeof(C) + o->matrix_bytes(sizeof(C));
+                grp_flops[g] += o->hx_flops() + 8.0 * double(nlen[c]);
+            }
+        }
+    };
+    regroup_counts();
+    // one level of the recurrence for group g on its stream
+    auto level = [&](int g, int kk) {
+        const int na = int(gcols[g].size());
+        if (na == 0) return;
+        cudaStream_t s = gs[g];
+        const int* cl = gcols_d[g].p;
+        double* pt = gpart[g].p;
         {
-            ProfScope ps("cf_apply", st, apply_bytes, apply_flops);
+            ProfScope ps("cf_apply", s, grp_bytes[g], grp_flops[g]);
             bool done_hub = false;
             if constexpr (hub) {
-                const dim3 g(gridA.x, unsigned(nact));
+                const dim3 gg(gridA.x, unsigned(na));
                 if (rows && fx) {
                     auto x = reinterpret_cast<const double2*>(vk);
                     auto xm = reinterpret_cast<const double2*>(vkm1);
                     auto y = reinterpret_cast<double2*>(wv);
                     auto kern = multi ? (sgn ? k_cf_apply_hub_fx<true, true> : k_cf_apply_hub_fx<true, false>)
                                       : (sgn ? k_cf_apply_hub_fx<false, true> : k_cf_apply_hub_fx<false, false>);
-                    kern<<<g, fx_threads, hub_smem, st>>>(view, hv.p, colq.p, x, xm, y, ld, cols.p, cf, part.p);
+                    kern<<<gg, fx_threads, hub_smem, s>>>(view, hv.p, colq.p, x, xm, y, ld, cl, cf, pt);
+                    done_hub = true;
+                } else if (rows && pair && cpc == 2) {
+                    auto x = reinterpret_cast<const float2*>(vk);
+                    auto xm = reinterpret_cast<const float2*>(vkm1);
+                    auto y = reinterpret_cast<float2*>(wv);
+                    auto kern = sgn ? k_cf_apply_hub_f2x2c2<true> : k_cf_apply_hub_f2x2c2<false>;
+                    const dim3 g2(gridA.x, unsigned((na + 1) / 2));
+                    kern<<<g2, kApplyThreads, hub_smem, s>>>(hviews[0], x, xm, y, ld, cl, na, cf, pt);
                     done_hub = true;
                 } else if (rows && pair) {
                     auto x = reinterpret_cast<const float2*>(vk);
@@ -1287,39 +1514,42 @@ static void cf_impl(const CFColumns& P, const View& view, const double* w, int n
                     auto y = reinterpret_cast<float2*>(wv);
                     auto kern = multi ? (sgn ? k_cf_apply_hub_f2x2<true, true> : k_cf_apply_hub_f2x2<true, false>)
                                       : (sgn ? k_cf_apply_hub_f2x2<false, true> : k_cf_apply_hub_f2x2<false, false>);
-                    kern<<<g, kApplyThreads, hub_smem, st>>>(view, hv.p, colq.p, x, xm, y, ld, cols.p, cf, part.p);
+                    kern<<<gg, kApplyThreads, hub_smem, s>>>(view, hv.p, colq.p, x, xm, y, ld, cl, cf, pt);
                     done_hub = true;
                 } else if (rows) {
                     // FP32 with an odd D_dn (FP64 always takes the fixed-point kernel)
                     if constexpr (std::is_same<C, float2>::value) {
                         if (multi)
-                            k_cf_apply_hub<C, true><<<g, kApplyThreads, hub_smem, st>>>(view, hv.p, colq.p, vk, vkm1,
-                                                                                        wv, ld, cols.p, cf, part.p);
+                            k_cf_apply_hub<C, true><<<gg, kApplyThreads, hub_smem, s>>>(view, hv.p, colq.p, vk, vkm1,
+                                                                                         wv, ld, cl, cf, pt);
                         else
-                            k_cf_apply_hub<C, false><<<g, kApplyThreads, hub_smem, st>>>(view, hv.p, colq.p, vk, vkm1,
-                                                                                         wv, ld, cols.p, cf, part.p);
+                            k_cf_apply_hub<C, false><<<gg, kApplyThreads, hub_smem, s>>>(view, hv.p, colq.p, vk, vkm1,
+                                                                                          wv, ld, cl, cf, pt);
                         done_hub = true;
                     }
                 }
             }
             if (!done_hub)
-                k_cf_apply_gen<View, C><<<dim3(grid, nact), 256, 0, st>>>(view, vk, vkm1, wv, nlen[0], ld, cols.p,
-                                                                          cf, part.p);
+                k_cf_apply_gen<View, C><<<dim3(grid, na), 256, 0, s>>>(view, vk, vkm1, wv, nlen[0], ld, cl, cf, pt);
         }
         {
-            ProfScope ps("cf_reduce", st, 0, 0);
-            k_cf_reduce_a<<<nact, 256, 0, st>>>(part.p, rows ? nblkA : grid, cols.p, a.p, nv, k, cf);
+            ProfScope ps("cf_reduce", s, 0, 0);
+            k_cf_reduce_a<<<na, 256, 0, s>>>(pt, rows ? nblkA : grid, cl, a.p, nv, kk, cf);
         }
         {
-            ProfScope ps("cf_orth", st, 3.0 * act_elems * sizeof(C), 8.0 * act_elems);
-            k_cf_orth<C><<<dim3(grid, nact), 256, 0, st>>>(vk, wv, ld, cols.p, clen_d.p, cf, part.p);
+            ProfScope ps("cf_orth", s, 3.0 * grp_elems[g] * sizeof(C), 8.0 * grp_elems[g]);
+            k_cf_orth<C><<<dim3(grid, na), 256, 0, s>>>(vk, wv, ld, cl, clen_d.p, cf, pt);
         }
         {
-            ProfScope ps("cf_reduce", st, 0, 0);
-            k_cf_reduce_b<<<nact, 256, 0, st>>>(part.p, grid, cols.p, b.p, nv, k, cf);
+            ProfScope ps("cf_reduce", s, 0, 0);
+            k_cf_reduce_b<<<na, 256, 0, s>>>(pt, grid, cl, b.p, nv, kk, cf);
         }
         out.launches += 4;
-        out.matvecs += nact;
+        out.matvecs += na;
+    };
+    int k = 0;
+    while (nact > 0 && k < maxdepth) {
+        for (int g = 0; g < ngrp; ++g) level(g, k);
         MSB_LAUNCH_CHECK();
         // (V_{k-1}, V_k, W) <- (V_k, W, V_{k-1})
         C* t = vkm1;
@@ -1328,7 +1558,12 @@ static void cf_impl(const CFColumns& P, const View& view, const double* w, int n
         wv = t;
         ++k;
         if (k % check == 0 || k == maxdepth) {
+            if (ngrp == 2) {                        // the groups meet: st waits for the second stream
+                MSB_CUDA(cudaEventRecord(gev, gs[1]));
+                MSB_CUDA(cudaStreamWaitEvent(st, gev, 0));
+            }
             for (int i = 0; i < nact; ++i) hdepth[hcols[i]] = k;
+            cols.upload(hcols.data(), std::max(nact, 1), st);
             {
                 ProfScope ps("cf_eval", st, 0, 40.0 * nact * n_w * double(k - k_eval));
                 k_cf_eval<<<nact, 128, 0, st>>>(a.p, b.p, nv, n0.p, cols.p, k_eval, k, E0d.p, wdev.p, n_w, eta,
@@ -1345,11 +1580,9 @@ static void cf_impl(const CFColumns& P, const View& view, const double* w, int n
                 if (k > check && hdiff[2 * c] <= cf_tol * hdiff[2 * c + 1]) fin = true;
                 if (!fin) hcols[keep++] = c;
             }
-            if (keep != nact) {
-                nact = keep;
-                recount();
-            }
-            cols.upload(hcols.data(), std::max(nact, 1), st);
+            nact = keep;
+            split();
+            regroup_counts();
         }
     }
     MSB_CUDA(cudaMemcpyAsync(I_out, I.p, size_t(nv) * n_w * sizeof(double),

@@ -68,3 +68,29 @@ def test_fp64_accurate_run_keeps_one_seed(cuda):
     ref = np.array([spla.spsolve((A - s * sp.identity(n)).tocsc(), b) for s in SHIFTS])
     err = np.linalg.norm(x.cpu().numpy() - ref, axis=1) / np.linalg.norm(ref, axis=1)
     assert err.max() <= 1e-8
+
+
+def test_fp32_round_off_triggers_a_reseed(cuda):
+    """FP32-mixed on the L = 8 ring, 41 incident energies, seeded at the far end of the grid
+    (w_in = 12): round-off leaves the true residual of the shifts at the resonance above a
+    tight reseed tolerance while their recursive residuals converged.  The solver rejects
+    them, reseeds at the rejected shift nearest the first seed, and that reseeded run
+    repairs at least one of them.  Every solution stays within 1e-4 of the oracle's
+    independent solve."""
+    from paper_2506_09551_gb300 import api
+    om, E_G, A, b = _system(8, 4, 4)
+    w_in = np.linspace(-4.0, 12.0, 41)
+    nb = np.linalg.norm(b)
+    rtol = 3e-6
+    kw = dict(tol=1e-7, maxit=5000, seed_index=40)
+    _, per1, seeds1, _, _ = _gpu(8, 4, 4, E_G, b, w_in, api.FP32_MIXED, reseed_tol=1.0, max_seeds=1, **kw)
+    rejected1 = [k for k in range(len(w_in)) if not per1["converged"][k] or per1["dr"][k] > rtol * nb]
+    assert per1["converged"].all() and rejected1
+    x, per, seeds, info, st = _gpu(8, 4, 4, E_G, b, w_in, api.FP32_MIXED, reseed_tol=rtol, max_seeds=4, **kw)
+    assert seeds[0] == 40 and len(seeds) >= 2
+    assert seeds[1] == min(rejected1, key=lambda k: abs(w_in[k] - w_in[40]))
+    assert per["accepted"].sum() > len(w_in) - len(rejected1)
+    n = A.shape[0]
+    ref = np.array([spla.spsolve((A - s * sp.identity(n)).tocsc(), b) for s in w_in])
+    err = np.linalg.norm(x.cpu().numpy().astype(np.complex128) - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    assert err.max() <= 1e-4, err.max()
