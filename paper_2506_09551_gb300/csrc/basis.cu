@@ -175,7 +175,10 @@ RowLayout row_layout(const std::vector<int32_t>& table, const std::vector<uint8_
         return z ^ (z >> 31);
     };
     std::vector<int32_t> touched;
-    const int64_t trials = 300 * D;
+    // simulated annealing over swaps: a worsening swap is taken with probability
+    // exp(-delta / T), the temperature falling to zero over the trials
+    const int64_t trials = 1000 * D;
+    const double T0 = 0.6;
     for (int64_t t = 0; t < trials; ++t) {
         const int32_t x = int32_t(rnd() % uint64_t(D)), y = int32_t(rnd() % uint64_t(D));
         const int bx = pos[x] & 15, by = pos[y] & 15;
@@ -196,7 +199,14 @@ RowLayout row_layout(const std::vector<int32_t>& table, const std::vector<uint8_
             touched.push_back(si);
         }
         for (int32_t si : touched) delta += long(setmax(si)) - long(cur[si]);
-        if (delta <= 0) {
+        bool take = delta <= 0;
+        if (!take) {
+            const double f = 1.0 - double(t) / double(trials);
+            const double T = T0 * f * f;
+            const double u = double(rnd() >> 11) * (1.0 / 9007199254740992.0);
+            take = T > 0 && u < std::exp(-double(delta) / T);
+        }
+        if (take) {
             for (int32_t si : touched) cur[si] = setmax(si);
             std::swap(pos[x], pos[y]);
             total += double(delta);

@@ -1365,10 +1365,11 @@ static void cf_impl(const CFColumns& P, const View& view, const double* w, int n
             const int t = tuned_cf_threads(maxDdn, maxDup, MSB_FP64);
             if (t == 128 || t == 256) fx_threads = t;
         }
-        // FP32: two columns per CTA by default (the autotuner may choose one)
+        // FP32: one column per CTA unless the autotuner measured two as faster (two
+        // columns halve the index work but cut the resident warps from 48 to 32 per SM)
         if (!multi && pair && hviews[0].slot16 != nullptr) {
             const int t = tuned_cf_threads(maxDdn, maxDup, MSB_FP32_MIXED);
-            cpc = (t == 1) ? 1 : 2;
+            cpc = (t == 2) ? 2 : 1;
         }
         fx = fx && rows;
         pair = pair && rows;
