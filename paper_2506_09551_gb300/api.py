@@ -360,11 +360,11 @@ def autotune(m: N.msb_model, prec: int, n_in: int):
     the library for later calls.  Returns a dict."""
     blk, thr = C.c_int(), C.c_int()
     bms = np.zeros(5, dtype=np.float64)
-    cms = np.zeros(2, dtype=np.float64)
+    cms = np.zeros(3, dtype=np.float64)
     N.check(N.load().msb_autotune(C.byref(m), prec, n_in, C.byref(blk), C.byref(thr),
                                   bms.ctypes.data_as(C.POINTER(C.c_double)), cms.ctypes.data_as(C.POINTER(C.c_double)),
                                   _stream()))
-    cands = (128, 256) if prec == FP64 else (1, 2)
+    cands = (128, 256) if prec == FP64 else (1, 2, 3)
     return {"block": blk.value, "cf_threads": thr.value,
             "ms_per_iteration": dict(zip((1, 2, 4, 8, 16), bms.tolist())),
             "ms_per_level": dict(zip(cands, cms.tolist()))}

@@ -1,7 +1,9 @@
 // Autotuner of the launch choices that leave the results unchanged (up to the
 // rounding of a block reduction): the lag B of the fused per-shift update of the
-// multi-shift solve (1, 2, 4, 8, 16 iterations per flush), and the threads per CTA
-// of the FP64 row-tiled continued-fraction apply (128 or 256).  Each candidate is
+// multi-shift solve (1, 2, 4, 8, 16 iterations per flush), and the shape of the
+// row-tiled continued-fraction apply: threads per CTA in FP64 (128 or 256); in FP32
+// one column per CTA at 6 CTAs per SM, two columns per CTA, or one column at 8 CTAs
+// per SM.  Each candidate is
 // timed on the model's own operators with CUDA events, as the difference between
 // a run of 2K and a run of K iterations (or levels), so that the allocations of a
 // call cancel.  The fastest choice is cached per problem shape and used by every
@@ -66,7 +68,7 @@ __global__ void k_tune_fill(C* v, int64_t n, uint64_t seed) {
 struct TuneOut {
     int block = 0, cf_threads = 0;
     double block_ms[5] = {0, 0, 0, 0, 0};
-    double cf_ms[2] = {0, 0};
+    double cf_ms[3] = {0, 0, 0};
 };
 
 template <typename C>
@@ -143,9 +145,10 @@ static void autotune_impl(const msb_model& m, msb_precision prec, int n_in, Tune
         k_tune_fill<C><<<grid_for(int64_t(n_in) * D, 256, 4), 256, 0, st>>>(phi.p, int64_t(n_in) * D, 0xCF11ull);
         std::vector<double> w(8), I(size_t(n_in) * 8);
         for (int i = 0; i < 8; ++i) w[i] = double(i);
-        const int Ts[2] = {prec == MSB_FP64 ? 128 : 1, prec == MSB_FP64 ? 256 : 2};
+        const int nT = prec == MSB_FP64 ? 2 : 3;
+        const int Ts[3] = {prec == MSB_FP64 ? 128 : 1, prec == MSB_FP64 ? 256 : 2, 3};
         double best = 1e300;
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < nT; ++i) {
             g_cf_threads_force = Ts[i];
             auto run = [&](int depth) {
                 CFResult cr;
@@ -193,7 +196,7 @@ extern "C" msb_status msb_autotune(const msb_model* model, msb_precision prec, i
         if (block) *block = out.block;
         if (cf_threads) *cf_threads = out.cf_threads;
         if (block_ms) for (int i = 0; i < 5; ++i) block_ms[i] = out.block_ms[i];
-        if (cf_ms) for (int i = 0; i < 2; ++i) cf_ms[i] = out.cf_ms[i];
+        if (cf_ms) for (int i = 0; i < 3; ++i) cf_ms[i] = out.cf_ms[i];
     });
 }
 

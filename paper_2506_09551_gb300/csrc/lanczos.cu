@@ -798,7 +798,8 @@ __global__ void __launch_bounds__(256, 5) k_cf_apply_hub_fx(HubView h0, const Hu
     if (threadIdx.x == 0) part[int64_t(blockIdx.y) * gridDim.x + blockIdx.x] = acc[0];
 }
 
-// FP32 pass A with two adjacent elements per thread: the up-spin gathers, the
+// FP32 pass A with two adjacent elements per thread (MINB CTAs per SM: 6 at 40
+// registers, or 8 at 32 registers for full occupancy): the up-spin gathers, the
 // V_{k-1} loads and the W stores move 16 bytes (two complex floats) at a time,
 // and the down-spin table is read as 16-bit entries, two per 32-bit load.
 // Needs an even Ddn (rows start on 16-byte boundaries) and Ddn < 32768.  The row
@@ -807,8 +808,8 @@ __global__ void __launch_bounds__(256, 5) k_cf_apply_hub_fx(HubView h0, const Hu
 // largest hop count, empty slots reading the zero kept past the row.  No FP64
 // instruction: coefficients arrive as FP32 copies, the product is compensated
 // FP32, and the block sum is float-float.
-template <bool Multi, bool Signed>
-__global__ void __launch_bounds__(256, 6) k_cf_apply_hub_f2x2(HubView h0, const HubView* __restrict__ hv,
+template <bool Multi, bool Signed, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_cf_apply_hub_f2x2(HubView h0, const HubView* __restrict__ hv,
                                                               const int* __restrict__ colq,
                                                               const float2* __restrict__ Vk,
                                                               const float2* __restrict__ Vkm1, float2* __restrict__ W,
@@ -822,10 +823,8 @@ __global__ void __launch_bounds__(256, 6) k_cf_apply_hub_f2x2(HubView h0, const 
         if (threadIdx.x == 0) part[int64_t(blockIdx.y) * gridDim.x + blockIdx.x] = 0.0;
         return;
     }
-    const int L = h.L;
     extern __shared__ __align__(16) unsigned char sm_raw[];
     float2* row = reinterpret_cast<float2*>(sm_raw);                // Ddn values of row u, then two zeros
-    float* lut = reinterpret_cast<float*>(row + h.Ddn + 2);        // 3 (L + 1) diagonal values * sig
     __shared__ int s_uoff[kMaxHops];
     __shared__ float s_usg[kMaxHops];
     __shared__ float red[64];
@@ -859,10 +858,6 @@ __global__ void __launch_bounds__(256, 6) k_cf_apply_hub_f2x2(HubView h0, const 
         }
         if (threadIdx.x == 0) reinterpret_cast<float4*>(row)[half] = make_float4(0.f, 0.f, 0.f, 0.f);   // row[Ddn], row[Ddn + 1]
     }
-    for (int i = threadIdx.x; i < 3 * (L + 1); i += blockDim.x) {
-        const int p = i % (L + 1), nb = i / (L + 1);
-        lut[i] = sig * (h.Uf * float(p) - h.Ucf * float(nb));
-    }
     if (threadIdx.x < nu) {
         const int32_t ent = __ldg(h.hup + int64_t(threadIdx.x) * h.Dup + u);
         s_uoff[threadIdx.x] = ((ent >> 1) * Ddn) >> 1;           // in float4 units
@@ -872,6 +867,7 @@ __global__ void __launch_bounds__(256, 6) k_cf_apply_hub_f2x2(HubView h0, const 
     const int core = h.core;
     const int ubits = core >= 0 ? int((su >> core) & 1u) : 0;
     const float mt = -h.tf * sig;
+    const float sU = sig * h.Uf, sUc = sig * h.Ucf;                 // diagonal: sig (U popc - Uc nb)
     const float mcB = -cB;
     const float4* __restrict__ Vc4 = reinterpret_cast<const float4*>(Vc);
     const uint32_t* __restrict__ t32 = reinterpret_cast<const uint32_t*>(placed ? h.hdn16p : h.hdn16);
@@ -927,8 +923,8 @@ __global__ void __launch_bounds__(256, 6) k_cf_apply_hub_f2x2(HubView h0, const 
         const uint2 sd = __ldg(sd2 + q);
         const int nb0 = core >= 0 ? ubits + int((sd.x >> core) & 1u) : 0;
         const int nb1 = core >= 0 ? ubits + int((sd.y >> core) & 1u) : 0;
-        const float dg0 = lut[__popc(su & sd.x) + nb0 * (L + 1)];
-        const float dg1 = lut[__popc(su & sd.y) + nb1 * (L + 1)];
+        const float dg0 = fmaf(sU, float(__popc(su & sd.x)), -sUc * float(nb0));
+        const float dg1 = fmaf(sU, float(__popc(su & sd.y)), -sUc * float(nb1));
         float2 x0, x1;
         if (placed) {                                           // own values: from global (L1/L2)
             const float4 xv = Vc4[(rbase >> 1) + q];
@@ -1365,11 +1361,12 @@ static void cf_impl(const CFColumns& P, const View& view, const double* w, int n
             const int t = tuned_cf_threads(maxDdn, maxDup, MSB_FP64);
             if (t == 128 || t == 256) fx_threads = t;
         }
-        // FP32: one column per CTA unless the autotuner measured two as faster (two
-        // columns halve the index work but cut the resident warps from 48 to 32 per SM)
+        // FP32 shape: 1 = one column per CTA at 6 CTAs per SM; 2 = two columns per CTA
+        // (half the index work, 4 CTAs per SM); 3 = one column at 8 CTAs per SM (32
+        // registers).  Shape 1 unless the autotuner measured another as faster.
         if (!multi && pair && hviews[0].slot16 != nullptr) {
             const int t = tuned_cf_threads(maxDdn, maxDup, MSB_FP32_MIXED);
-            cpc = (t == 2) ? 2 : 1;
+            cpc = (t == 2 || t == 3) ? t : 1;
         }
         fx = fx && rows;
         pair = pair && rows;
@@ -1385,14 +1382,19 @@ static void cf_impl(const CFColumns& P, const View& view, const double* w, int n
                 if (hub_smem > 200 * 1024) {               // rows too long for two per CTA
                     cpc = 1;
                     hub_smem = (maxDdn + 2) * int64_t(sizeof(C)) + 3 * (maxL + 1) * 8;
-                    fn = sgn ? (const void*)k_cf_apply_hub_f2x2<false, true> : (const void*)k_cf_apply_hub_f2x2<false, false>;
+                    fn = sgn ? (const void*)k_cf_apply_hub_f2x2<false, true, 6> : (const void*)k_cf_apply_hub_f2x2<false, false, 6>;
                 }
-            } else if (pair)
-                fn = multi ? (sgn ? (const void*)k_cf_apply_hub_f2x2<true, true> : (const void*)k_cf_apply_hub_f2x2<true, false>)
-                           : (sgn ? (const void*)k_cf_apply_hub_f2x2<false, true> : (const void*)k_cf_apply_hub_f2x2<false, false>);
+            } else if (pair && cpc == 3)
+                fn = sgn ? (const void*)k_cf_apply_hub_f2x2<false, true, 8> : (const void*)k_cf_apply_hub_f2x2<false, false, 8>;
+            else if (pair)
+                fn = multi ? (sgn ? (const void*)k_cf_apply_hub_f2x2<true, true, 6> : (const void*)k_cf_apply_hub_f2x2<true, false, 6>)
+                           : (sgn ? (const void*)k_cf_apply_hub_f2x2<false, true, 6> : (const void*)k_cf_apply_hub_f2x2<false, false, 6>);
             else
                 fn = multi ? (const void*)k_cf_apply_hub<float2, true> : (const void*)k_cf_apply_hub<float2, false>;
             MSB_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(hub_smem)));
+            if (cpc == 3)      // eight rows of shared memory per SM: take the largest carve-out
+                MSB_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                              int(cudaSharedmemCarveoutMaxShared)));
         }
     }
     MSB_REQUIRE(!multi || rows, "a batch of clusters needs the row-tiled Hubbard apply (one hopping amplitude)");
@@ -1513,8 +1515,9 @@ static void cf_impl(const CFColumns& P, const View& view, const double* w, int n
                     auto x = reinterpret_cast<const float2*>(vk);
                     auto xm = reinterpret_cast<const float2*>(vkm1);
                     auto y = reinterpret_cast<float2*>(wv);
-                    auto kern = multi ? (sgn ? k_cf_apply_hub_f2x2<true, true> : k_cf_apply_hub_f2x2<true, false>)
-                                      : (sgn ? k_cf_apply_hub_f2x2<false, true> : k_cf_apply_hub_f2x2<false, false>);
+                    auto kern = cpc == 3 ? (sgn ? k_cf_apply_hub_f2x2<false, true, 8> : k_cf_apply_hub_f2x2<false, false, 8>)
+                                : multi ? (sgn ? k_cf_apply_hub_f2x2<true, true, 6> : k_cf_apply_hub_f2x2<true, false, 6>)
+                                        : (sgn ? k_cf_apply_hub_f2x2<false, true, 6> : k_cf_apply_hub_f2x2<false, false, 6>);
                     kern<<<gg, kApplyThreads, hub_smem, s>>>(view, hv.p, colq.p, x, xm, y, ld, cl, cf, pt);
                     done_hub = true;
                 } else if (rows) {
