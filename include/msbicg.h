@@ -171,20 +171,27 @@ void msb_basis_destroy(msb_basis *b);
  * L < 3. */
 msb_status msb_basis_row_order(const msb_basis *b, int periodic, uint16_t *order);
 
-/* Shared-memory placement of a down-spin row used by the FP32 continued-fraction
- * apply.  That kernel stages each row of a vector in shared memory (in the row
- * order above) and gathers the down-spin hop targets from it; since the hop
- * table is the same for every row, the library places position p at a slot
- * chosen once per sector, so that the gathers of a half-warp hit fewer
- * shared-memory bank conflicts (a deterministic hill climb; no effect on any
- * result).  Host only, no device.
+/* Shared-memory placement and hop schedule of a down-spin row used by the FP32
+ * continued-fraction apply.  That kernel stages each row of a vector in shared
+ * memory (in the row order above) and gathers the down-spin hop targets from
+ * it, one hop per position per round, for the largest hop count of the warp's
+ * positions.  Since the hop table is the same for every row, the library
+ * chooses once per sector (deterministic searches; no effect on any result
+ * beyond the order of a sum) the slot of each position and the round of each
+ * of its hops, so that the gathers of a half-warp hit fewer shared-memory bank
+ * conflicts.  Host only, no device.
  * slot: HOST array of D_dn entries (may be NULL): slot[p] for each position p
- * (a permutation of 0..D_dn-1).  cost_plain / cost_layout (may be NULL): the
- * mean worst-bank count per half-warp gather for slot[p] = p and for the
- * chosen slots (1 is conflict free).  Errors: MSB_EINVAL if D_dn is odd or
- * not below 32768, or periodic with L < 3. */
-msb_status msb_basis_row_layout(const msb_basis *b, int periodic, uint16_t *slot, double *cost_plain,
-                                double *cost_layout);
+ * (a permutation of 0..D_dn-1).  width (may be NULL): the table width W, the
+ * number of bonds (L for a ring, L - 1 for an open chain).  hops: HOST array of
+ * W x D_dn entries (may be NULL): hops[k * D_dn + p] = (target position << 1 |
+ * sign bit) read by position p in round k, or D_dn << 1 for an idle round (the
+ * zero word); every hop of p appears once in rounds below its warp's largest
+ * hop count.  cost_plain / cost_layout (may be NULL): the mean worst-bank
+ * count per half-warp gather for slot[p] = p with the hops in table order, and
+ * for the chosen slots and rounds (1 is conflict free).  Errors: MSB_EINVAL if
+ * D_dn is odd or not below 32768, or periodic with L < 3. */
+msb_status msb_basis_row_layout(const msb_basis *b, int periodic, uint16_t *slot, int *width, uint16_t *hops,
+                                double *cost_plain, double *cost_layout);
 
 /* ------------------------------------------------------------------------ */
 /* Operators A = H, H' (matrix-free) or a user CSR matrix                    */
@@ -346,13 +353,17 @@ msb_status msb_multishift_bicg_reseeded(msb_op *A, msb_complex c0, const void *b
  * Krylov space: two operator applications per iteration per shift, against one
  * per iteration for all shifts in msb_multishift_bicg_solve.  b: device vector;
  * x: device block of n_shifts vectors (output).  HOST outputs (may be NULL):
- * iters[k], resid[k] (recursive ||r_k|| / ||b||), converged[k].
- * info->matvecs = 2 * sum_k iters[k]; info->iterations = max_k iters[k].
+ * iters[k], resid[k] (recursive ||r_k|| / ||b||), converged[k], restarts[k].
+ * A shift whose recurrence breaks down (<r^|v> or <r^|r> vanishing, omega = 0,
+ * a non-finite scalar) restarts from its current iterate with r = r^ = b - A_k x
+ * (one more product), at most 64 times.
+ * info->matvecs = 2 * sum_k iters[k] + sum_k restarts[k];
+ * info->iterations = max_k iters[k].
  * Allocates four n_shifts x dim work blocks.  Returns MSB_EMAXITER (results
  * written) if a shift did not converge within maxit or broke down. */
 msb_status msb_bicgstab_solve(msb_op *A, msb_complex c0, const void *b, const msb_complex *shifts, int n_shifts,
                               double tol, int maxit, msb_precision prec, void *x, int *iters, double *resid,
-                              int *converged, msb_solve_info *info, void *stream);
+                              int *converged, int *restarts, msb_solve_info *info, void *stream);
 
 /* ------------------------------------------------------------------------ */
 /* Second step: batched Lanczos continued fraction (Eq. 1; Sec. III)         */

@@ -83,10 +83,11 @@ def row_order(L: int, n_dn: int, periodic: bool = True):
         lib.msb_basis_destroy(h)
 
 
-def row_layout(L: int, n_dn: int, periodic: bool = True):
+def row_layout(L: int, n_dn: int, periodic: bool = True, hops: bool = False):
     """Shared-memory slot of each row position (in the continued-fraction row order) used
     by the FP32 continued-fraction apply, and the mean worst-bank count per half-warp
-    gather without / with it."""
+    gather without / with it.  hops=True also returns the scheduled hop table (W x D:
+    target position << 1 | sign bit per round, D << 1 for an idle round)."""
     lib = N.load()
     h = C.c_void_p()
     N.check(lib.msb_basis_create(L, 0, n_dn, C.byref(h)))
@@ -94,10 +95,16 @@ def row_layout(L: int, n_dn: int, periodic: bool = True):
         dd = C.c_int64()
         N.check(lib.msb_basis_dims(h, None, C.byref(dd), None))
         slot = np.zeros(dd.value, dtype=np.uint16)
+        width = C.c_int()
         c0, c1 = C.c_double(), C.c_double()
         N.check(lib.msb_basis_row_layout(h, 1 if periodic else 0, slot.ctypes.data_as(C.POINTER(C.c_uint16)),
-                                         C.byref(c0), C.byref(c1)))
-        return slot, c0.value, c1.value
+                                         C.byref(width), None, C.byref(c0), C.byref(c1)))
+        if not hops:
+            return slot, c0.value, c1.value
+        tab = np.zeros((width.value, dd.value), dtype=np.uint16)
+        N.check(lib.msb_basis_row_layout(h, 1 if periodic else 0, None, None,
+                                         tab.ctypes.data_as(C.POINTER(C.c_uint16)), None, None))
+        return slot, c0.value, c1.value, tab
     finally:
         lib.msb_basis_destroy(h)
 
@@ -212,14 +219,16 @@ class Operator:
         iters = np.zeros(ns, dtype=np.int32)
         resid = np.zeros(ns, dtype=np.float64)
         conv = np.zeros(ns, dtype=np.int32)
+        restarts = np.zeros(ns, dtype=np.int32)
         info = N.msb_solve_info()
         c0 = complex(c0)
         st = N.load().msb_bicgstab_solve(
             self.h, N.msb_complex(c0.real, c0.imag), _ptr(b.to(cdtype(prec)).contiguous()), sh, ns, tol, maxit, prec,
             _ptr(x), iters.ctypes.data_as(C.POINTER(C.c_int)), resid.ctypes.data_as(C.POINTER(C.c_double)),
-            conv.ctypes.data_as(C.POINTER(C.c_int)), C.byref(info), _stream())
+            conv.ctypes.data_as(C.POINTER(C.c_int)), restarts.ctypes.data_as(C.POINTER(C.c_int)), C.byref(info),
+            _stream())
         N.check(st, allow=allow_status)
-        return x, dict(iters=iters, resid=resid, converged=conv.astype(bool)), info.as_dict(), st
+        return x, dict(iters=iters, resid=resid, converged=conv.astype(bool), restarts=restarts), info.as_dict(), st
 
     def multishift_reseeded(self, b: torch.Tensor, shifts, c0: complex = 0.0, tol: float = 1e-10,
                             maxit: int = 5000, reseed_tol: float = 1e-8, seed_index: int = 0, max_seeds: int = 8,

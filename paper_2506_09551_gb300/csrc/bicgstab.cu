@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(256) k_bcg_norm(const V* __restrict__ b, int64
 }
 
 struct BcgResult {
-    std::vector<int> iters, conv;
+    std::vector<int> iters, conv, restarts;
     std::vector<double> resid;
     int max_iters = 0;
     int64_t matvecs = 0, launches = 0;
@@ -338,11 +338,13 @@ static void bicgstab_impl(const msb_op* op, const View& view, double2 c0, const 
     out.iters.resize(ns);
     out.conv.resize(ns);
     out.resid.resize(ns);
+    out.restarts.resize(ns);
     out.matvecs = 0;
     for (int k = 0; k < ns; ++k) {
         out.iters[k] = hs[k].iters;
         out.conv[k] = hs[k].conv;
         out.resid[k] = out.bnorm > 0 ? hs[k].rnorm / out.bnorm : 0.0;
+        out.restarts[k] = hs[k].restarts;
         out.max_iters = std::max(out.max_iters, hs[k].iters);
         out.matvecs += 2 * int64_t(hs[k].iters) + hs[k].restarts;
     }
@@ -352,8 +354,8 @@ static void bicgstab_impl(const msb_op* op, const View& view, double2 c0, const 
 
 extern "C" msb_status msb_bicgstab_solve(msb_op* A, msb_complex c0, const void* b, const msb_complex* shifts,
                                          int n_shifts, double tol, int maxit, msb_precision prec, void* x,
-                                         int* iters, double* resid, int* converged, msb_solve_info* info,
-                                         void* stream) {
+                                         int* iters, double* resid, int* converged, int* restarts,
+                                         msb_solve_info* info, void* stream) {
     msb_status result = MSB_OK;
     msb_status g = msb::guard("msb_bicgstab_solve", [&] {
         msb::require_device();
@@ -385,6 +387,7 @@ extern "C" msb_status msb_bicgstab_solve(msb_op* A, msb_complex c0, const void* 
             if (iters) iters[k] = out.iters[k];
             if (resid) resid[k] = out.resid[k];
             if (converged) converged[k] = out.conv[k];
+            if (restarts) restarts[k] = out.restarts[k];
             nconv += out.conv[k];
             mx = std::max(mx, out.resid[k]);
         }

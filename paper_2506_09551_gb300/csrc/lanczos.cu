@@ -824,7 +824,7 @@ __global__ void __launch_bounds__(256, MINB) k_cf_apply_hub_f2x2(HubView h0, con
         return;
     }
     extern __shared__ __align__(16) unsigned char sm_raw[];
-    float2* row = reinterpret_cast<float2*>(sm_raw);                // Ddn values of row u, then two zeros
+    float2* row = reinterpret_cast<float2*>(sm_raw);                // Ddn values of row u, then kRowZeroWords zeros
     __shared__ int s_uoff[kMaxHops];
     __shared__ float s_usg[kMaxHops];
     __shared__ float red[64];
@@ -856,7 +856,8 @@ __global__ void __launch_bounds__(256, MINB) k_cf_apply_hub_f2x2(HubView h0, con
             float4* dst = reinterpret_cast<float4*>(row);
             for (int i = threadIdx.x; i < half; i += blockDim.x) dst[i] = src[i];
         }
-        if (threadIdx.x == 0) reinterpret_cast<float4*>(row)[half] = make_float4(0.f, 0.f, 0.f, 0.f);   // row[Ddn], row[Ddn + 1]
+        if (threadIdx.x < kRowZeroWords / 2)                   // row[Ddn .. Ddn + kRowZeroWords - 1]
+            reinterpret_cast<float4*>(row)[half + threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     if (threadIdx.x < nu) {
         const int32_t ent = __ldg(h.hup + int64_t(threadIdx.x) * h.Dup + u);
@@ -980,9 +981,9 @@ __global__ void __launch_bounds__(256, 4) k_cf_apply_hub_f2x2c2(HubView h, const
     const int Ddn = int(h.Ddn);
     const int half = Ddn >> 1;
     extern __shared__ __align__(16) unsigned char sm_raw[];
-    float2* row0 = reinterpret_cast<float2*>(sm_raw);               // row u of column 0, then two zeros
-    float2* row1 = row0 + (Ddn + 2);                                // row u of column 1, then two zeros
-    float* lut0 = reinterpret_cast<float*>(row1 + (Ddn + 2));       // 3 (L + 1) diagonal values * sig, per column
+    float2* row0 = reinterpret_cast<float2*>(sm_raw);               // row u of column 0, then kRowZeroWords zeros
+    float2* row1 = row0 + (Ddn + kRowZeroWords);                    // row u of column 1, then kRowZeroWords zeros
+    float* lut0 = reinterpret_cast<float*>(row1 + (Ddn + kRowZeroWords));   // 3 (L + 1) diagonal values * sig, per column
     float* lut1 = lut0 + 3 * (L + 1);
     __shared__ int s_uoff[kMaxHops];
     __shared__ float s_usg[kMaxHops];
@@ -1009,9 +1010,9 @@ __global__ void __launch_bounds__(256, 4) k_cf_apply_hub_f2x2c2(HubView h, const
             row1[sp & 0xFFFFu] = make_float2(b.x, b.y);
             row1[sp >> 16] = make_float2(b.z, b.w);
         }
-        if (threadIdx.x == 0) {
-            reinterpret_cast<float4*>(row0)[half] = make_float4(0.f, 0.f, 0.f, 0.f);
-            reinterpret_cast<float4*>(row1)[half] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (threadIdx.x < kRowZeroWords / 2) {
+            reinterpret_cast<float4*>(row0)[half + threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
+            reinterpret_cast<float4*>(row1)[half + threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
     }
     for (int i = threadIdx.x; i < 3 * (L + 1); i += blockDim.x) {
@@ -1350,7 +1351,10 @@ static void cf_impl(const CFColumns& P, const View& view, const double* w, int n
             pair = pair && h.Ddn % 2 == 0;
             sgn = sgn || h.usign || h.dsign;
         }
-        hub_smem = (maxDdn + 2) * int64_t(sizeof(C)) + 3 * (maxL + 1) * 8;   // row, two zero slots, table
+        // row, its zero words (one for the FP64 and generic kernels, one per bank pair for
+        // the FP32 two-element kernels, padded to 16 bytes), diagonal table
+        const int zw = pair ? kRowZeroWords : 2;
+        hub_smem = (maxDdn + zw) * int64_t(sizeof(C)) + 3 * (maxL + 1) * 8;
         rows = rows && hub_smem <= 160 * 1024;
         // FP64 fixed-point kernel: rows of up to 1024 elements take 128-thread CTAs (~7
         // elements per thread at L = 12, so the staging barrier and the block reduction
@@ -1378,10 +1382,10 @@ static void cf_impl(const CFColumns& P, const View& view, const double* w, int n
                            : (sgn ? (const void*)k_cf_apply_hub_fx<false, true> : (const void*)k_cf_apply_hub_fx<false, false>);
             else if (pair && cpc == 2) {
                 fn = sgn ? (const void*)k_cf_apply_hub_f2x2c2<true> : (const void*)k_cf_apply_hub_f2x2c2<false>;
-                hub_smem = 2 * (maxDdn + 2) * int64_t(sizeof(C)) + 2 * 3 * (maxL + 1) * 4;
+                hub_smem = 2 * (maxDdn + zw) * int64_t(sizeof(C)) + 2 * 3 * (maxL + 1) * 4;
                 if (hub_smem > 200 * 1024) {               // rows too long for two per CTA
                     cpc = 1;
-                    hub_smem = (maxDdn + 2) * int64_t(sizeof(C)) + 3 * (maxL + 1) * 8;
+                    hub_smem = (maxDdn + zw) * int64_t(sizeof(C)) + 3 * (maxL + 1) * 8;
                     fn = sgn ? (const void*)k_cf_apply_hub_f2x2<false, true, 6> : (const void*)k_cf_apply_hub_f2x2<false, false, 6>;
                 }
             } else if (pair && cpc == 3)

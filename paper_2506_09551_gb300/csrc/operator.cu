@@ -85,18 +85,20 @@ static void build_hubbard(msb_op* op, const msb_model& m, int intermediate) {
         for (size_t i = 0; i < tpos.size(); ++i) t16[i] = tpos[i] < 0 ? empty : uint16_t(tpos[i]);
         op->hdn16.alloc(t16.size());
         op->hdn16.upload(t16.data(), t16.size());
-        if (D % 2 == 0 && D >= 2) {
-            // targets moved to their shared-memory slots for the FP32 row-tiled apply
+        if (D % 2 == 0 && D >= 2 && D + kRowZeroWords < 32768) {
+            // targets moved to their shared-memory slots, hops in their scheduled rounds,
+            // for the FP32 row-tiled apply
             const RowLayout& lay = cached_row_layout(m.L, op->sec_dn, m.periodic != 0, kApplyThreads, m.lx);
             MSB_REQUIRE(int64_t(lay.perm.size()) == D, "row layout size mismatch");
+            // entries in the layout's round order (the same hops per position)
+            MSB_REQUIRE(lay.table.size() == tpos.size(), "row schedule size mismatch");
             std::vector<uint16_t> tp(tpos.size());
             for (size_t i = 0; i < tpos.size(); ++i) {
-                if (tpos[i] < 0) { tp[i] = empty; continue; }
-                const int32_t t = tpos[i] >> 1;
-                MSB_REQUIRE(t >= 0 && t < D, "hop target out of range");
-                tp[i] = uint16_t((int32_t(lay.perm[t]) << 1) | (tpos[i] & 1));
+                const int32_t e = lay.table[i];
+                const int32_t t = e >> 1;
+                MSB_REQUIRE(t >= 0 && t < D + kRowZeroWords, "hop target out of range");
+                tp[i] = t >= D ? uint16_t(e) : uint16_t((int32_t(lay.perm[t]) << 1) | (e & 1));   // zero words stay
             }
-            for (uint16_t v : tp) MSB_REQUIRE((v >> 1) <= D, "permuted hop entry out of range");
             op->hdn16p.alloc(tp.size());
             op->hdn16p.upload(tp.data(), tp.size());
             op->slot16.alloc(lay.perm.size());

@@ -288,11 +288,18 @@ struct msb_op {
 namespace msb {
 // Threads per CTA of the row-tiled continued-fraction apply kernels.
 constexpr int kApplyThreads = 256;
-// Shared-memory slot of each down-spin element for the FP32 row-tiled apply
-// (basis.cu): perm[d] = slot of element d; costs = mean worst-bank count per
-// half-warp gather, plain layout and chosen layout.
+// Zero words kept past a row staged in shared memory by the FP32 row-tiled
+// apply, one on each of the 16 bank pairs (idle hop rounds read one of them).
+constexpr int kRowZeroWords = 16;
+// Shared-memory slot of each down-spin position and the round of each of its
+// hops for the FP32 row-tiled apply (basis.cu): perm[p] = slot of position p;
+// table[k * D + p] = the position-space entry (target << 1 | sign) position p
+// reads in round k, a target D + b naming zero word b; costs = mean worst-bank count per
+// half-warp gather, identity slots in hop order and the chosen layout.
 struct RowLayout {
     std::vector<uint16_t> perm;
+    std::vector<int32_t> table;
+    int width = 0;
     double cost_plain = 0, cost_layout = 0;
 };
 RowLayout row_layout(const std::vector<int32_t>& table, const std::vector<uint8_t>& count, int64_t D, int W,

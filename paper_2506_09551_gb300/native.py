@@ -69,7 +69,7 @@ SIGNATURES = {
     "msb_basis_states": (_I, [_P, _I, C.POINTER(C.c_uint32)]),
     "msb_basis_destroy": (None, [_P]),
     "msb_op_create_hubbard": (_I, [C.POINTER(msb_model), _I, C.POINTER(_P)]),
-    "msb_basis_row_layout": (_I, [_P, _I, C.POINTER(C.c_uint16), _PD, _PD]),
+    "msb_basis_row_layout": (_I, [_P, _I, C.POINTER(C.c_uint16), _PI, C.POINTER(C.c_uint16), _PD, _PD]),
     "msb_basis_row_order": (_I, [_P, _I, C.POINTER(C.c_uint16)]),
     "msb_op_create_csr": (_I, [_I64, C.POINTER(C.c_int64), C.POINTER(C.c_int32), _PD, C.POINTER(_P)]),
     "msb_op_create_direct_sum": (_I, [C.POINTER(_P), _PD, _I, C.POINTER(_P)]),
@@ -85,7 +85,7 @@ SIGNATURES = {
     "msb_multishift_bicg_dual_solve": (_I, [_P, msb_complex, _P, C.POINTER(msb_complex), _I, _D, _I, _I, _I, _P,
                                             _PI, _PD, _PI, C.POINTER(msb_solve_info), _P]),
     "msb_bicgstab_solve": (_I, [_P, msb_complex, _P, C.POINTER(msb_complex), _I, _D, _I, _I, _P, _PI, _PD, _PI,
-                                C.POINTER(msb_solve_info), _P]),
+                                _PI, C.POINTER(msb_solve_info), _P]),
     "msb_autotune": (_I, [C.POINTER(msb_model), _I, _I, _PI, _PI, _PD, _PD, _P]),
     "msb_autotune_forget": (None, []),
     "msb_multishift_bicg_reseeded": (_I, [_P, msb_complex, _P, C.POINTER(msb_complex), _I, _D, _I, _I, _I, _D, _I,
