@@ -639,6 +639,15 @@ def gpu_arm(args, rank, world):
             return api.rixs_map_sites(m, p, sites, w_in, w)
         return api.rixs_map_ops(H, Hp, p, w_in, w, out=out)
 
+    # launch choices measured on this GPU before the warm-up (untimed): the lag of the
+    # per-shift update and the shape of the continued-fraction apply, cached by the
+    # library for the maps below
+    tuned = None
+    if not args.no_autotune and not (n_q or clusters or sites):
+        t_at = time.perf_counter()
+        tuned = api.autotune(m, prec, len(w_in))
+        tuned["seconds"] = time.perf_counter() - t_at
+        print(f"[bench] autotune: {tuned}", file=sys.stderr, flush=True)
     for _ in range(args.warmup):
         one_map()
     torch.cuda.synchronize()
@@ -763,6 +772,7 @@ def gpu_arm(args, rank, world):
         "h_apply_alg_gbs": h_gbs,
         "clocks": clocks,
         "precision_comparison": precision_cmp,
+        "autotune": tuned,
         "profiled_step": "kernel shares and roofline from one extra map with the library profiler on",
         "solve": {k: infos[-1][k] for k in ("iterations", "n_converged", "matvecs", "cf_depth_max",
                                             "cf_depth_min", "seconds_ground_state", "seconds_solve",
@@ -835,6 +845,7 @@ def main():
     ap.add_argument("--no-clocks", action="store_true", help="do not sample nvidia-smi (profiling runs)")
     ap.add_argument("--n-in", type=int, default=0, help="incident energies (0: the workload's; profiling runs)")
     ap.add_argument("--no-fp64-leg", action="store_true", help="skip the FP64 form of an FP32-mixed workload")
+    ap.add_argument("--no-autotune", action="store_true", help="fixed launch choices (no trials before the warm-up)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))

@@ -408,16 +408,19 @@ msb_status msb_rixs_map(const msb_model *model, const msb_map_params *params,
  * B in {1, 2, 4, 8, 16} of the fused per-shift update of a solve with n_in
  * shifts (FP32 or FP64 per `prec`), and the shape of the row-tiled
  * continued-fraction apply: threads per CTA (128 or 256) for MSB_FP64; for
- * MSB_FP32_MIXED 1 (one column per CTA, 6 CTAs per SM), 2 (two columns per CTA)
- * or 3 (one column, 8 CTAs per SM), returned in *cf_threads.  Each candidate is
+ * MSB_FP32_MIXED 1 (one column per CTA, 6 CTAs per SM), 2 (two columns per CTA),
+ * 3 (one column, 8 CTAs per SM) or 4 (one column per 512-thread CTA, 4 CTAs per
+ * SM), returned in *cf_threads.  Each candidate is
  * timed with CUDA events as the difference of a 2K- and a K-iteration run (the
- * allocations of a call cancel).  The fastest choices are cached for the whole
+ * allocations of a call cancel); an apply shape is taken only if its
+ * 32-level continued fraction agrees with the first shape's (relative L2 1e-10
+ * in FP64, 1e-4 in FP32).  The fastest choices are cached for the whole
  * process, keyed by the problem's shape (intermediate dimension, n_in and
  * precision for B; row length, row count and precision for the threads), and
  * used by every later call that leaves them automatic (params->block or the
  * solver's `block` = 0).  HOST outputs (may be NULL): the choices, and the
  * measured milliseconds per iteration for each B (5 values) and per level for
- * each apply shape (3 values; the third is 0 for FP64).  Allocates and frees its own work
+ * each apply shape (4 values; the last two are 0 for FP64).  Allocates and frees its own work
  * vectors; synchronises `stream`.  The paper has no counterpart. */
 msb_status msb_autotune(const msb_model *model, msb_precision prec, int n_in, int *block, int *cf_threads,
                         double *block_ms, double *cf_ms, void *stream);

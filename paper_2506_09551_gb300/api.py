@@ -365,15 +365,15 @@ def rixs_map(m: N.msb_model, params: N.msb_map_params, w_in, w, G: torch.Tensor 
 
 def autotune(m: N.msb_model, prec: int, n_in: int):
     """Timed trials of the per-shift update lag and of the continued-fraction apply's shape
-    (FP64: threads per CTA; FP32: columns per CTA) on this model; the choices are cached by
+    (FP64: threads per CTA; FP32: shape 1-4) on this model; the choices are cached by
     the library for later calls.  Returns a dict."""
     blk, thr = C.c_int(), C.c_int()
     bms = np.zeros(5, dtype=np.float64)
-    cms = np.zeros(3, dtype=np.float64)
+    cms = np.zeros(4, dtype=np.float64)
     N.check(N.load().msb_autotune(C.byref(m), prec, n_in, C.byref(blk), C.byref(thr),
                                   bms.ctypes.data_as(C.POINTER(C.c_double)), cms.ctypes.data_as(C.POINTER(C.c_double)),
                                   _stream()))
-    cands = (128, 256) if prec == FP64 else (1, 2, 3)
+    cands = (128, 256) if prec == FP64 else (1, 2, 3, 4)
     return {"block": blk.value, "cf_threads": thr.value,
             "ms_per_iteration": dict(zip((1, 2, 4, 8, 16), bms.tolist())),
             "ms_per_level": dict(zip(cands, cms.tolist()))}

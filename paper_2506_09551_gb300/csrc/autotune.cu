@@ -2,11 +2,12 @@
 // rounding of a block reduction): the lag B of the fused per-shift update of the
 // multi-shift solve (1, 2, 4, 8, 16 iterations per flush), and the shape of the
 // row-tiled continued-fraction apply: threads per CTA in FP64 (128 or 256); in FP32
-// one column per CTA at 6 CTAs per SM, two columns per CTA, or one column at 8 CTAs
-// per SM.  Each candidate is
+// one column per CTA at 6 CTAs per SM, two columns per CTA, one column at 8 CTAs
+// per SM, or one column per 512-thread CTA.  Each candidate is
 // timed on the model's own operators with CUDA events, as the difference between
 // a run of 2K and a run of K iterations (or levels), so that the allocations of a
-// call cancel.  The fastest choice is cached per problem shape and used by every
+// call cancel; an apply shape whose fraction disagrees with the first shape's
+// beyond rounding is not taken.  The fastest choice is cached per problem shape and used by every
 // call that leaves the choice on automatic (params->block == 0 for B; always for
 // the apply threads).
 #include <chrono>
@@ -68,7 +69,8 @@ __global__ void k_tune_fill(C* v, int64_t n, uint64_t seed) {
 struct TuneOut {
     int block = 0, cf_threads = 0;
     double block_ms[5] = {0, 0, 0, 0, 0};
-    double cf_ms[3] = {0, 0, 0};
+    double cf_ms[4] = {0, 0, 0, 0};
+    int cf_ok[4] = {0, 0, 0, 0};
 };
 
 template <typename C>
@@ -139,14 +141,18 @@ static void autotune_impl(const msb_model& m, msb_precision prec, int n_in, Tune
         }
     }
     // 2. the row-tiled continued-fraction apply: threads per CTA (FP64: 128 or 256) or
-    // columns per CTA (FP32: 1 or 2)
+    // the FP32 shape (1..4)
     {
         DevBuf<C> phi(size_t(n_in) * D);
         k_tune_fill<C><<<grid_for(int64_t(n_in) * D, 256, 4), 256, 0, st>>>(phi.p, int64_t(n_in) * D, 0xCF11ull);
         std::vector<double> w(8), I(size_t(n_in) * 8);
         for (int i = 0; i < 8; ++i) w[i] = double(i);
-        const int nT = prec == MSB_FP64 ? 2 : 3;
-        const int Ts[3] = {prec == MSB_FP64 ? 128 : 1, prec == MSB_FP64 ? 256 : 2, 3};
+        const int nT = prec == MSB_FP64 ? 2 : 4;
+        const int Ts[4] = {prec == MSB_FP64 ? 128 : 1, prec == MSB_FP64 ? 256 : 2, 3, 4};
+        // a shape is taken only if its 32-level fraction agrees with the first shape's
+        // (the shapes differ only in the order of a block sum)
+        const double agree = prec == MSB_FP64 ? 1e-10 : 1e-4;
+        std::vector<double> I0;
         double best = 1e300;
         for (int i = 0; i < nT; ++i) {
             g_cf_threads_force = Ts[i];
@@ -165,7 +171,15 @@ static void autotune_impl(const msb_model& m, msb_precision prec, int n_in, Tune
                 throw;
             }
             g_cf_threads_force = 0;
-            if (out.cf_ms[i] < best) { best = out.cf_ms[i]; out.cf_threads = Ts[i]; }
+            double num = 0, den = 0;
+            if (i == 0) I0 = I;
+            for (size_t j = 0; j < I.size(); ++j) {
+                num += (I[j] - I0[j]) * (I[j] - I0[j]);
+                den += I0[j] * I0[j];
+            }
+            const bool ok = std::isfinite(num) && num <= agree * agree * den;
+            out.cf_ok[i] = ok ? 1 : 0;
+            if (ok && out.cf_ms[i] < best) { best = out.cf_ms[i]; out.cf_threads = Ts[i]; }
         }
     }
     cudaEventDestroy(e0);
@@ -196,7 +210,7 @@ extern "C" msb_status msb_autotune(const msb_model* model, msb_precision prec, i
         if (block) *block = out.block;
         if (cf_threads) *cf_threads = out.cf_threads;
         if (block_ms) for (int i = 0; i < 5; ++i) block_ms[i] = out.block_ms[i];
-        if (cf_ms) for (int i = 0; i < 3; ++i) cf_ms[i] = out.cf_ms[i];
+        if (cf_ms) for (int i = 0; i < 4; ++i) cf_ms[i] = out.cf_ms[i];
     });
 }
 

@@ -798,8 +798,9 @@ __global__ void __launch_bounds__(256, 5) k_cf_apply_hub_fx(HubView h0, const Hu
     if (threadIdx.x == 0) part[int64_t(blockIdx.y) * gridDim.x + blockIdx.x] = acc[0];
 }
 
-// FP32 pass A with two adjacent elements per thread (MINB CTAs per SM: 6 at 40
-// registers, or 8 at 32 registers for full occupancy): the up-spin gathers, the
+// FP32 pass A with two adjacent elements per thread (NT threads, MINB CTAs per SM:
+// 256 x 6 at 40 registers, 256 x 8 or 512 x 4 at 32 registers for full occupancy;
+// a row takes less shared memory per resident warp with 512): the up-spin gathers, the
 // V_{k-1} loads and the W stores move 16 bytes (two complex floats) at a time,
 // and the down-spin table is read as 16-bit entries, two per 32-bit load.
 // Needs an even Ddn (rows start on 16-byte boundaries) and Ddn < 32768.  The row
@@ -808,8 +809,8 @@ __global__ void __launch_bounds__(256, 5) k_cf_apply_hub_fx(HubView h0, const Hu
 // largest hop count, empty slots reading the zero kept past the row.  No FP64
 // instruction: coefficients arrive as FP32 copies, the product is compensated
 // FP32, and the block sum is float-float.
-template <bool Multi, bool Signed, int MINB>
-__global__ void __launch_bounds__(256, MINB) k_cf_apply_hub_f2x2(HubView h0, const HubView* __restrict__ hv,
+template <bool Multi, bool Signed, int MINB, int NT = 256>
+__global__ void __launch_bounds__(NT, MINB) k_cf_apply_hub_f2x2(HubView h0, const HubView* __restrict__ hv,
                                                               const int* __restrict__ colq,
                                                               const float2* __restrict__ Vk,
                                                               const float2* __restrict__ Vkm1, float2* __restrict__ W,
@@ -1367,10 +1368,11 @@ static void cf_impl(const CFColumns& P, const View& view, const double* w, int n
         }
         // FP32 shape: 1 = one column per CTA at 6 CTAs per SM; 2 = two columns per CTA
         // (half the index work, 4 CTAs per SM); 3 = one column at 8 CTAs per SM (32
-        // registers).  Shape 1 unless the autotuner measured another as faster.
+        // registers); 4 = one column per 512-thread CTA, 4 per SM (32 registers).
+        // Shape 1 unless the autotuner measured another as faster.
         if (!multi && pair && hviews[0].slot16 != nullptr) {
             const int t = tuned_cf_threads(maxDdn, maxDup, MSB_FP32_MIXED);
-            cpc = (t == 2 || t == 3) ? t : 1;
+            cpc = (t >= 2 && t <= 4) ? t : 1;
         }
         fx = fx && rows;
         pair = pair && rows;
@@ -1390,6 +1392,9 @@ static void cf_impl(const CFColumns& P, const View& view, const double* w, int n
                 }
             } else if (pair && cpc == 3)
                 fn = sgn ? (const void*)k_cf_apply_hub_f2x2<false, true, 8> : (const void*)k_cf_apply_hub_f2x2<false, false, 8>;
+            else if (pair && cpc == 4)
+                fn = sgn ? (const void*)k_cf_apply_hub_f2x2<false, true, 4, 512>
+                         : (const void*)k_cf_apply_hub_f2x2<false, false, 4, 512>;
             else if (pair)
                 fn = multi ? (sgn ? (const void*)k_cf_apply_hub_f2x2<true, true, 6> : (const void*)k_cf_apply_hub_f2x2<true, false, 6>)
                            : (sgn ? (const void*)k_cf_apply_hub_f2x2<false, true, 6> : (const void*)k_cf_apply_hub_f2x2<false, false, 6>);
@@ -1519,10 +1524,13 @@ static void cf_impl(const CFColumns& P, const View& view, const double* w, int n
                     auto x = reinterpret_cast<const float2*>(vk);
                     auto xm = reinterpret_cast<const float2*>(vkm1);
                     auto y = reinterpret_cast<float2*>(wv);
-                    auto kern = cpc == 3 ? (sgn ? k_cf_apply_hub_f2x2<false, true, 8> : k_cf_apply_hub_f2x2<false, false, 8>)
-                                : multi ? (sgn ? k_cf_apply_hub_f2x2<true, true, 6> : k_cf_apply_hub_f2x2<true, false, 6>)
-                                        : (sgn ? k_cf_apply_hub_f2x2<false, true, 6> : k_cf_apply_hub_f2x2<false, false, 6>);
-                    kern<<<gg, kApplyThreads, hub_smem, s>>>(view, hv.p, colq.p, x, xm, y, ld, cl, cf, pt);
+                    auto kern = cpc == 4   ? (sgn ? k_cf_apply_hub_f2x2<false, true, 4, 512>
+                                                      : k_cf_apply_hub_f2x2<false, false, 4, 512>)
+                                : cpc == 3 ? (sgn ? k_cf_apply_hub_f2x2<false, true, 8> : k_cf_apply_hub_f2x2<false, false, 8>)
+                                : multi    ? (sgn ? k_cf_apply_hub_f2x2<true, true, 6> : k_cf_apply_hub_f2x2<true, false, 6>)
+                                           : (sgn ? k_cf_apply_hub_f2x2<false, true, 6> : k_cf_apply_hub_f2x2<false, false, 6>);
+                    kern<<<gg, cpc == 4 ? 512 : kApplyThreads, hub_smem, s>>>(view, hv.p, colq.p, x, xm, y, ld, cl, cf,
+                                                                            pt);
                     done_hub = true;
                 } else if (rows) {
                     // FP32 with an odd D_dn (FP64 always takes the fixed-point kernel)

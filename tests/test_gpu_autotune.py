@@ -22,7 +22,7 @@ def test_autotune_choices_are_used_and_leave_the_map_unchanged(cuda, prec):
     assert t["block"] in (1, 2, 4, 8, 16)
     assert all(v > 0 for v in t["ms_per_iteration"].values())
     assert all(v > 0 for v in t["ms_per_level"].values())
-    assert t["cf_threads"] in ((128, 256) if prec == 0 else (1, 2, 3))
+    assert t["cf_threads"] in ((128, 256) if prec == 0 else (1, 2, 3, 4))
     I_tuned, info_t, _ = api.rixs_map(m, api.map_params(precision=prec, block=0, **tol), wl.w_in, wl.w)
     I_expl, _, _ = api.rixs_map(m, api.map_params(precision=prec, block=t["block"], **tol), wl.w_in, wl.w)
     # the lag of the per-shift update is bitwise neutral; the CTA size only reorders a block sum
