@@ -886,6 +886,14 @@ __global__ void __launch_bounds__(NT, MINB) k_cf_apply_hub_f2x2(HubView h0, cons
         const int q = act ? q0 : 0;                             // elements d0 = 2q, d1 = 2q + 1
         float a0x = 0.f, a0y = 0.f, a1x = 0.f, a1y = 0.f;
         int e = 0;
+        if constexpr (!Signed) {                                // four partner rows in flight
+            for (; e + 4 <= nu; e += 4) {
+                const float4 v0 = Vc4[s_uoff[e] + q], v1 = Vc4[s_uoff[e + 1] + q];
+                const float4 v2 = Vc4[s_uoff[e + 2] + q], v3 = Vc4[s_uoff[e + 3] + q];
+                a0x += (v0.x + v1.x) + (v2.x + v3.x); a0y += (v0.y + v1.y) + (v2.y + v3.y);
+                a1x += (v0.z + v1.z) + (v2.z + v3.z); a1y += (v0.w + v1.w) + (v2.w + v3.w);
+            }
+        }
         for (; e + 2 <= nu; e += 2) {
             const float4 v = Vc4[s_uoff[e] + q], w4 = Vc4[s_uoff[e + 1] + q];
             if constexpr (Signed) {
