@@ -370,20 +370,23 @@ def job_throughput(units_per_rank: float, world: int, seconds: float) -> float:
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
-def measured_traffic(workload, kernel, alg_bytes_per_launch):
-    """DRAM bytes per launch scaled from an ncu capture of the same kernel (None if none)."""
+def measured_traffic(workload, kernel, alg_bytes_per_launch, shape=None):
+    """DRAM bytes per launch scaled from an ncu capture of the same kernel (None if none,
+    or if the capture was of another launch shape than the one that ran)."""
     try:
         with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
             rec = json.load(f)[workload][kernel]
     except (OSError, KeyError, ValueError):
         return None
+    if shape is not None and rec.get("shape") not in (None, shape):
+        return None
     return rec["dram_bytes"] / rec["alg_bytes"] * alg_bytes_per_launch
 
 
-def dominant_roofline(stats, prec, peaks, workload=None):
+def dominant_roofline(stats, prec, peaks, workload=None, shape=None):
     top = max(stats, key=lambda s: s["ms"])
     avg_ms = top["ms"] / top["launches"]
-    traffic = measured_traffic(workload, top["name"], top["alg_bytes"] / top["launches"])
+    traffic = measured_traffic(workload, top["name"], top["alg_bytes"] / top["launches"], shape)
     if prec == 0 and top["name"] != "cf_apply":
         # FP64 complex multiply-adds per shift (the per-shift update): FP64-pipe bound
         achieved = top["alg_flops"] / top["launches"] / (avg_ms * 1e-3) / 1e12
@@ -737,7 +740,11 @@ def gpu_arm(args, rank, world):
               f"map difference {precision_cmp['rel_l2_mixed_vs_fp64']:.2e}", file=sys.stderr, flush=True)
 
     peaks = measured_peaks()
-    top, roof = dominant_roofline(stats, prec, peaks, args.workload)
+    # the continued-fraction apply shape that ran: the autotuned one, else the default
+    # (FP32 shape 1; FP64 128 threads for rows up to 1024, else 256)
+    ddn = math.comb(wl.L, wl.n_dn)
+    shape = tuned["cf_threads"] if tuned and tuned.get("cf_threads") else (1 if prec else (128 if ddn <= 1024 else 256))
+    top, roof = dominant_roofline(stats, prec, peaks, args.workload, shape)
     total_ms = sum(s["ms"] for s in stats)
     apply_cls = [s for s in stats if s["name"] in ("cf_apply", "seed_mvm", "h_apply")]
     h_gbs = (sum(s["alg_bytes"] for s in apply_cls) / (sum(s["ms"] for s in apply_cls) * 1e-3) / 1e9

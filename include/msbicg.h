@@ -414,7 +414,8 @@ msb_status msb_rixs_map(const msb_model *model, const msb_map_params *params,
  * timed with CUDA events as the difference of a 2K- and a K-iteration run (the
  * allocations of a call cancel); an apply shape is taken only if its
  * 32-level continued fraction agrees with the first shape's (relative L2 1e-10
- * in FP64, 1e-4 in FP32).  The fastest choices are cached for the whole
+ * in FP64, 1e-4 in FP32), and the fixed default shape is kept unless another is
+ * at least 2% faster.  The fastest choices are cached for the whole
  * process, keyed by the problem's shape (intermediate dimension, n_in and
  * precision for B; row length, row count and precision for the threads), and
  * used by every later call that leaves them automatic (params->block or the

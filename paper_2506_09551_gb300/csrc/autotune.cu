@@ -7,7 +7,8 @@
 // timed on the model's own operators with CUDA events, as the difference between
 // a run of 2K and a run of K iterations (or levels), so that the allocations of a
 // call cancel; an apply shape whose fraction disagrees with the first shape's
-// beyond rounding is not taken.  The fastest choice is cached per problem shape and used by every
+// beyond rounding is not taken, and the default shape is kept unless another is
+// at least 2% faster.  The fastest choice is cached per problem shape and used by every
 // call that leaves the choice on automatic (params->block == 0 for B; always for
 // the apply threads).
 #include <chrono>
@@ -181,6 +182,11 @@ static void autotune_impl(const msb_model& m, msb_precision prec, int n_in, Tune
             out.cf_ok[i] = ok ? 1 : 0;
             if (ok && out.cf_ms[i] < best) { best = out.cf_ms[i]; out.cf_threads = Ts[i]; }
         }
+        // the fixed default (FP32 shape 1; FP64 128 threads for rows up to 1024, else
+        // 256) stays unless another shape is at least 2% faster: closer timings are
+        // within run-to-run noise
+        const int d = prec == MSB_FP64 && Ddn > 1024 ? 1 : 0;
+        if (out.cf_ok[d] && out.cf_threads != Ts[d] && best > 0.98 * out.cf_ms[d]) out.cf_threads = Ts[d];
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
