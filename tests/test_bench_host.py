@@ -38,3 +38,22 @@ def test_reference_arm_unavailable_line():
     assert out.returncode == 0, out.stderr
     line = json.loads(out.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference" and "unavailable" in line
+
+
+def test_traffic_only_for_the_captured_launch_shape():
+    """The measured DRAM traffic of a capture scales to the bench's launches only when the
+    bench ran the launch shape that was captured."""
+    import json
+    import bench
+    rec = json.load(open(os.path.join(ROOT, "profiles", "ncu_traffic.json")))
+    for wl, shape in (("hubbard-L14-mixed", 1), ("hubbard-L12-fp64", 128)):
+        r = rec[wl]["cf_apply"]
+        assert r["shape"] == shape and r["dram_bytes"] > 0
+        t = bench.measured_traffic(wl, "cf_apply", 1e9, shape)
+        assert t == r["dram_bytes"] / r["alg_bytes"] * 1e9
+        # DRAM bytes over algorithmic bytes: below 1 where the captured columns' V_k stays
+        # in L2 across the launch (the 8-column L = 12 capture), above 1 for partner rows
+        # evicted and read again (L = 14)
+        assert 0.8 <= t / 1e9 < 1.3
+        assert bench.measured_traffic(wl, "cf_apply", 1e9, shape + 1) is None
+    assert bench.measured_traffic("no-such-workload", "cf_apply", 1e9, 1) is None
