@@ -118,7 +118,7 @@ def _check_layout(L, n, periodic):
     return slot, c_plain, c_layout
 
 
-@pytest.mark.parametrize("L,n", [(8, 4), (10, 5), (12, 6)])
+@pytest.mark.parametrize("L,n", [(8, 4), (10, 5), (12, 6), (14, 7)])
 def test_layout_and_schedule(L, n):
     from paper_2506_09551_gb300 import api
     slot, c_plain, c_layout = _check_layout(L, n, True)
